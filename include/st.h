@@ -1,0 +1,175 @@
+/*
+ * st.h -- C ABI of the GB300 space-time sparse-grid wave solver.
+ *
+ * The library solves the linear wave equation of Eq. (1),
+ *     d_t^2 u - div(c^2 grad u) = f in Omega x (0,T),  u = 0 on dOmega,
+ *     u(.,0) = u0, d_t u(.,0) = v0,
+ * on a box Omega in R^d (d = 1, 2, 3) with the conforming space-time Galerkin
+ * method of Section 2.2 (Eq. (9)): Q1 finite elements in space, C^1 quadratic
+ * splines in time with w(0) = 0, the exponentially weighted form of Eq. (6);
+ * and combines the anisotropic full-grid solutions with the +-1 coefficients of
+ * the combination formula, Eq. (19).
+ *
+ * Levels: level j means 2^j uniform cells per direction on the box (space) or
+ * 2^j uniform intervals on (0,T) (time).  The component set of Eq. (19) is
+ *   (mx + a, mt + J - a, +1), a = 0..J,   (mx + a - 1, mt + J - a, -1), a = 1..J,
+ * ordered as listed (all +1 terms by increasing spatial level, then all -1 terms).
+ *
+ * Data discretisation (the same reading as the reference oracle): c^2 is
+ * sampled at cell centres and held constant per cell; u0, v0 and the spatial
+ * factors of f are replaced by their Q1 nodal interpolants at each
+ * component's spatial level; time integrals use 8-point Gauss-Legendre per
+ * time interval.
+ *
+ * Memory: the handle owns every device buffer it uses.  Callbacks are called
+ * only inside st_setup and their data is copied.  Output buffers passed to
+ * st_combine / st_component_coeffs are owned by the caller.  All GPU work is
+ * enqueued on the stream given in st_options (0 = legacy default stream).
+ * A handle is not thread safe; use one handle per host thread and stream.
+ *
+ * Errors: every call returns an st_status; st_last_error(h) returns a static
+ * or handle-owned message for the last failure on that handle (or on handle
+ * creation when h is NULL).  No call aborts the process.
+ */
+#ifndef ST_H_
+#define ST_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_ARG = 1,            /* invalid argument or unsupported size */
+  ST_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  ST_ERR_OOM = 3,            /* device allocation failed */
+  ST_ERR_NOT_CONVERGED = 4,  /* an iterative solve hit its iteration limit */
+  ST_ERR_STATE = 5,          /* call out of order (e.g. combine before solve) */
+  ST_ERR_CALLBACK = 6,       /* a user callback returned non-zero */
+  ST_ERR_NUMERIC = 7         /* NaN/Inf or a breakdown in a factorisation */
+} st_status;
+
+typedef enum { ST_FP64 = 0, ST_FP32_IR = 1 } st_precision;
+
+/* Vectorised data callbacks.  pts is n x d, point-major (x0 y0 z0 x1 y1 ...).
+ * They write n values to out and return 0 on success. */
+typedef int (*st_space_fn)(int64_t n, const double* pts, double* out, void* user);
+typedef int (*st_time_fn)(int64_t n, const double* t, double* out, void* user);
+typedef int (*st_spacetime_fn)(int64_t n, const double* pts, double t, double* out, void* user);
+
+typedef struct {
+  st_space_fn fn;  /* NULL = the zero function */
+  void* user;
+} st_field;
+
+/* One separable source term g(x) s(t) of f. */
+typedef struct {
+  st_space_fn g;
+  void* g_user;
+  st_time_fn s;
+  void* s_user;
+} st_source_term;
+
+/* The problem of Eq. (1) with the combination levels of Eq. (19). */
+typedef struct {
+  int d;                    /* space dimension, 1..3 */
+  double lo[3], hi[3];      /* box Omega = prod (lo_k, hi_k) */
+  double T;                 /* final time, > 0 */
+  st_field c2;              /* c^2(x) > 0, sampled at cell centres (required) */
+  int n_terms;              /* number of separable source terms */
+  const st_source_term* terms;
+  st_spacetime_fn f_general; /* optional non-separable part f(x,t); NULL = 0 */
+  void* f_user;
+  st_field u0, v0;          /* initial displacement and velocity (NULL = 0) */
+  int J;                    /* combination level J >= 0 */
+  int mx, mt;               /* coarsest spatial / temporal levels */
+} st_problem;
+
+typedef struct {
+  int precision;    /* st_precision */
+  double tol;       /* target normwise backward error of each component,
+                       ||F - S U|| / (||S|| ||U|| + ||F||) (0 = default 1e-14) */
+  int max_iter;     /* inner Krylov iteration limit per mode (0 = default) */
+  int max_sweeps;   /* refinement sweeps per component (0 = default) */
+  void* stream;     /* cudaStream_t */
+} st_options;
+
+typedef struct {
+  int jx, jt, coef;         /* levels and combination coefficient */
+  int64_t n_space, n_time;  /* dim V_jx, dim V_jt */
+  int method;               /* 0 = time eigenbasis, 1 = space eigenbasis */
+  int n_modes;              /* spatial problems solved per sweep */
+} st_component_info;
+
+typedef struct {
+  int sweeps;               /* refinement sweeps taken */
+  int max_inner_iters;      /* largest inner Krylov count over modes and sweeps */
+  double rel_residual;      /* final ||F - S U|| / ||F|| (FP64, 2-norms) */
+  double backward_error;    /* final ||F - S U|| / (||S|| ||U|| + ||F||), ||S|| bounded above */
+  int status;               /* st_status of this component */
+} st_solve_info;
+
+typedef struct st_handle st_handle;
+
+/* Build everything that depends only on the problem (levels, c^2, data):
+ * time matrices and their FP64 eigenbasis, spatial level hierarchy, sampled
+ * data, factorisations of the coarsest multigrid operators.  Reads the
+ * problem and its callbacks; copies what it needs. */
+st_status st_setup(const st_problem* problem, const st_options* options, st_handle** out);
+
+/* Number of components (2J+1) and their description, in component order. */
+st_status st_num_components(const st_handle* h, int* n);
+st_status st_component(const st_handle* h, int k, st_component_info* info);
+
+/* Solve component k (0 <= k < n), or all components when k == -1, Eq. (9).
+ * Asynchronous on the handle's stream unless info != NULL, in which case it
+ * synchronises and fills info (for k == -1, the worst component). */
+st_status st_solve_component(st_handle* h, int k, st_solve_info* info);
+
+/* Evaluate u^CF of Eq. (19) on the nodal target grid of spatial level jx_star
+ * and temporal level jt_star: (2^jx*+1)^d nodes (boundary included,
+ * lexicographic, x fastest) times 2^jt*+1 uniform times of [0,T] (time
+ * slowest).  out_dev: caller-owned device array of that many doubles.
+ * Requires every component to be solved (ST_ERR_STATE otherwise). */
+st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev);
+
+/* Copy the FP64 coefficient array U_k (n_time x n_space, time-major) of a
+ * solved component to caller-owned host memory. */
+st_status st_component_coeffs(st_handle* h, int k, double* host_out);
+
+/* Total space-time degrees of freedom of all components (N^sparse_DoFs). */
+st_status st_total_dofs(const st_handle* h, int64_t* dofs);
+
+/* Bytes this handle has copied host->device and device->host since creation
+ * (setup uploads, convergence flags and norms read back, component copies). */
+st_status st_transfer_bytes(const st_handle* h, int64_t* h2d, int64_t* d2h);
+
+/* Number of kernels this handle has launched since creation. */
+st_status st_kernel_launches(const st_handle* h, int64_t* count);
+
+/* Per-kernel-class timing.  st_profile(h, 1) clears the record and starts
+ * recording a CUDA event pair on the handle's stream around every kernel
+ * launch (extra launch overhead: use it for a separate measurement pass);
+ * st_profile(h, 0) stops.  st_profile_read synchronises and writes one
+ * entry per kernel class seen since the last st_profile call (at most
+ * max_out; *n_out receives the count): launches, summed event time, and the
+ * algorithmic bytes and flops of those launches. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double bytes;
+  double flops;
+} st_kernel_stat;
+st_status st_profile(st_handle* h, int enable);
+st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n_out);
+
+st_status st_destroy(st_handle* h);
+const char* st_last_error(const st_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ST_H_ */

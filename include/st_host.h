@@ -1,0 +1,39 @@
+/*
+ * st_host.h -- host-only building blocks of st_setup (no GPU needed).
+ *
+ * They expose the FP64 setup math of the library so that it can be checked on
+ * a machine without a GPU.  All arrays are caller-owned host memory, row-major.
+ * Every call returns ST_OK or ST_ERR_ARG (bad sizes) / ST_ERR_NUMERIC.
+ */
+#ifndef ST_HOST_H_
+#define ST_HOST_H_
+
+#include "st.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Time matrices of level jt on (0,T) (proof of Prop. 1, Section 4.1):
+ * A[i][j] = (psi_j'', psi_i')_e + psi_j'(0) psi_i'(0), B[i][j] = (psi_j, psi_i')_e,
+ * g1[i] = (1, psi_i')_e, d0[i] = psi_i'(0); n_t = 2^jt + 1. */
+st_status st_host_time_matrices(int jt, double T, double* A, double* B, double* g1, double* d0);
+
+/* Eigen-decomposition of B^{-1} A used by the time eigenbasis method: the
+ * kept eigenvalues (one of each conjugate pair, Im > 0, and the real ones),
+ * as interleaved (re, im) pairs in lam[2 * nsel] (caller provides 2 * n_t),
+ * the 1-norm condition estimate of the eigenvector matrix and the relative
+ * eigen-residual. */
+st_status st_host_time_eig(int jt, double T, int* nsel, double* lam, double* cond_est, double* resid);
+
+/* Component list of Eq. (19): out[3k .. 3k+2] = (j_x, j_t, coefficient), k < 2J+1. */
+st_status st_host_components(int J, int mx, int mt, int* out);
+
+/* Symmetric-definite K v = mu M v (n x n dense): mu[n], Phi[n x n] (columns
+ * are M-orthonormal eigenvectors). */
+st_status st_host_sym_gen_eig(int n, const double* K, const double* M, double* mu, double* Phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ST_HOST_H_ */

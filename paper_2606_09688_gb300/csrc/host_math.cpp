@@ -1,0 +1,524 @@
+// Host-side FP64 setup math.  See host_math.h for the definitions.
+#include "host_math.h"
+
+#include "bspline.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace st {
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Roots of the Legendre polynomial P_n by Newton's method from the
+  // asymptotic guesses cos(pi (i + 3/4) / (n + 1/2)); P_n and P_n' from the
+  // three-term recurrence (k+1) P_{k+1} = (2k+1) z P_k - k P_{k-1}.
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = std::acos(-1.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int bspline_span(int N, double T, double t) {
+  int k = (int)std::floor(t / (T / N));
+  return std::min(std::max(k, 0), N - 1);
+}
+
+void bspline_local(int N, double T, int k, double t, double val[3], double d1[3], double d2[3]) {
+  bs_local(N, T, k, t, val, d1, d2);
+}
+
+void build_time_level(int jt, double T, TimeLevel& tl) {
+  tl.jt = jt;
+  tl.N = 1 << jt;
+  tl.nt = tl.N + 1;
+  tl.T = T;
+  const int N = tl.N, nt = tl.nt;
+  const double h = T / N;
+  std::vector<double> gx, gw;
+  gauss_legendre(8, gx, gw);
+  const int nq = 8 * N;
+  tl.A.assign((size_t)nt * nt, 0.0);
+  tl.B.assign((size_t)nt * nt, 0.0);
+  tl.qt.assign(nq, 0.0);
+  tl.qw.assign(nq, 0.0);
+  tl.Q.assign((size_t)nt * nq, 0.0);
+  tl.g1.assign(nt, 0.0);
+  tl.d0.assign(nt, 0.0);
+  for (int k = 0; k < N; ++k) {
+    for (int q = 0; q < 8; ++q) {
+      const double t = k * h + 0.5 * (gx[q] + 1.0) * h;
+      const double wq = 0.5 * h * gw[q];
+      const double we = wq * std::exp(-t / T);
+      const int iq = k * 8 + q;
+      tl.qt[iq] = t;
+      tl.qw[iq] = wq;
+      double v[3], d1[3], d2[3];
+      bspline_local(N, T, k, t, v, d1, d2);
+      for (int a = 0; a < 3; ++a) {
+        const int i = k + a - 1;  // psi index (B_0 removed)
+        if (i < 0) continue;
+        tl.Q[(size_t)i * nq + iq] = we * d1[a];
+        tl.g1[i] += we * d1[a];
+        for (int b = 0; b < 3; ++b) {
+          const int j = k + b - 1;
+          if (j < 0) continue;
+          tl.A[(size_t)i * nt + j] += we * d1[a] * d2[b];
+          tl.B[(size_t)i * nt + j] += we * d1[a] * v[b];
+        }
+      }
+    }
+  }
+  double v[3], d1[3], d2[3];
+  bspline_local(N, T, 0, 0.0, v, d1, d2);
+  for (int a = 1; a < 3; ++a) tl.d0[a - 1] = d1[a];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) tl.A[(size_t)i * nt + j] += tl.d0[i] * tl.d0[j];
+}
+
+bool lu_solve_real(int n, std::vector<double> A, std::vector<double>& Bm, int nrhs) {
+  std::vector<int> piv(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[(size_t)i * n + k]) > std::fabs(A[(size_t)p * n + k])) p = i;
+    if (A[(size_t)p * n + k] == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+      for (int j = 0; j < nrhs; ++j) std::swap(Bm[(size_t)k * nrhs + j], Bm[(size_t)p * nrhs + j]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (l == 0.0) continue;
+      for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+      for (int j = 0; j < nrhs; ++j) Bm[(size_t)i * nrhs + j] -= l * Bm[(size_t)k * nrhs + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    for (int j = 0; j < nrhs; ++j) {
+      double s = Bm[(size_t)k * nrhs + j];
+      for (int i = k + 1; i < n; ++i) s -= A[(size_t)k * n + i] * Bm[(size_t)i * nrhs + j];
+      Bm[(size_t)k * nrhs + j] = s / A[(size_t)k * n + k];
+    }
+  return true;
+}
+
+bool lu_inverse_cplx(int n, std::vector<cplx> A, std::vector<cplx>& Ainv) {
+  Ainv.assign((size_t)n * n, cplx(0.0));
+  for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(A[(size_t)i * n + k]) > std::abs(A[(size_t)p * n + k])) p = i;
+    if (std::abs(A[(size_t)p * n + k]) == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)k * n + j], A[(size_t)p * n + j]);
+        std::swap(Ainv[(size_t)k * n + j], Ainv[(size_t)p * n + j]);
+      }
+    for (int i = k + 1; i < n; ++i) {
+      const cplx l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (l == cplx(0.0)) continue;
+      for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+      for (int j = 0; j < n; ++j) Ainv[(size_t)i * n + j] -= l * Ainv[(size_t)k * n + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    for (int j = 0; j < n; ++j) {
+      cplx s = Ainv[(size_t)k * n + j];
+      for (int i = k + 1; i < n; ++i) s -= A[(size_t)k * n + i] * Ainv[(size_t)i * n + j];
+      Ainv[(size_t)k * n + j] = s / A[(size_t)k * n + k];
+    }
+  return true;
+}
+
+// Givens rotation [c s; -conj(s) c] with real c that maps (a, b) to (r, 0).
+static void givens(cplx a, cplx b, double& c, cplx& s) {
+  const double aa = std::abs(a), bb = std::abs(b);
+  if (bb == 0.0) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  if (aa == 0.0) {
+    c = 0.0;
+    s = std::conj(b) / bb;
+    return;
+  }
+  const double nrm = std::hypot(aa, bb);
+  c = aa / nrm;
+  s = (a / aa) * std::conj(b) / nrm;
+}
+
+bool complex_schur(int n, std::vector<cplx>& H, std::vector<cplx>& Z) {
+  // Explicitly shifted QR iteration on an upper Hessenberg matrix, with
+  // Wilkinson shifts, deflation on negligible subdiagonal entries and
+  // exceptional shifts after 10 and 20 stagnant steps.
+  auto h = [&](int i, int j) -> cplx& { return H[(size_t)i * n + j]; };
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, iter = 0, total = 0;
+  std::vector<double> cs(n);
+  std::vector<cplx> sn(n);
+  while (hi > 0) {
+    int l = hi;
+    for (; l > 0; --l) {
+      const double scale = std::abs(h(l - 1, l - 1)) + std::abs(h(l, l));
+      if (std::abs(h(l, l - 1)) <= eps * (scale > 0 ? scale : 1.0)) {
+        h(l, l - 1) = 0.0;
+        break;
+      }
+    }
+    if (l == hi) {
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (++total > 60 * n) return false;
+    ++iter;
+    cplx mu;
+    if (iter % 10 == 0) {
+      mu = h(hi, hi) + 0.75 * std::abs(h(hi, hi - 1));
+    } else {
+      const cplx a = h(hi - 1, hi - 1), b = h(hi - 1, hi), c = h(hi, hi - 1), d = h(hi, hi);
+      const cplx half = 0.5 * (a - d);
+      const cplx disc = std::sqrt(half * half + b * c);
+      const cplx m1 = 0.5 * (a + d) + disc, m2 = 0.5 * (a + d) - disc;
+      mu = (std::abs(m1 - d) < std::abs(m2 - d)) ? m1 : m2;
+    }
+    for (int k = l; k <= hi; ++k) h(k, k) -= mu;
+    for (int k = l; k < hi; ++k) {
+      double c;
+      cplx s;
+      givens(h(k, k), h(k + 1, k), c, s);
+      cs[k] = c;
+      sn[k] = s;
+      for (int j = k; j < n; ++j) {
+        const cplx x = h(k, j), y = h(k + 1, j);
+        h(k, j) = c * x + s * y;
+        h(k + 1, j) = -std::conj(s) * x + c * y;
+      }
+    }
+    for (int k = l; k < hi; ++k) {
+      const double c = cs[k];
+      const cplx s = sn[k];
+      const int rmax = std::min(k + 2, hi);
+      for (int i = 0; i <= rmax; ++i) {
+        const cplx x = h(i, k), y = h(i, k + 1);
+        h(i, k) = c * x + std::conj(s) * y;
+        h(i, k + 1) = -s * x + c * y;
+      }
+      for (int i = 0; i < n; ++i) {
+        const cplx x = Z[(size_t)i * n + k], y = Z[(size_t)i * n + k + 1];
+        Z[(size_t)i * n + k] = c * x + std::conj(s) * y;
+        Z[(size_t)i * n + k + 1] = -s * x + c * y;
+      }
+    }
+    for (int k = l; k <= hi; ++k) h(k, k) += mu;
+  }
+  return true;
+}
+
+bool time_eig(const TimeLevel& tl, TimeEig& out) {
+  const int n = tl.nt;
+  // C = B^{-1} A
+  std::vector<double> C = tl.A;
+  if (!lu_solve_real(n, tl.B, C, n)) return false;
+  // Householder reduction to upper Hessenberg form, Q accumulated.
+  std::vector<double> Hm = C, Qm((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qm[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double alpha = 0.0;
+    for (int i = k + 1; i < n; ++i) alpha += Hm[(size_t)i * n + k] * Hm[(size_t)i * n + k];
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    if (Hm[(size_t)(k + 1) * n + k] > 0) alpha = -alpha;
+    std::fill(v.begin(), v.end(), 0.0);
+    for (int i = k + 1; i < n; ++i) v[i] = Hm[(size_t)i * n + k];
+    v[k + 1] -= alpha;
+    double vn = 0.0;
+    for (int i = k + 1; i < n; ++i) vn += v[i] * v[i];
+    if (vn == 0.0) continue;
+    // H <- (I - 2vv^T/vn) H (I - 2vv^T/vn);  Q <- Q (I - 2vv^T/vn)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k + 1; i < n; ++i) s += v[i] * Hm[(size_t)i * n + j];
+      s *= 2.0 / vn;
+      for (int i = k + 1; i < n; ++i) Hm[(size_t)i * n + j] -= s * v[i];
+    }
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += Hm[(size_t)i * n + j] * v[j];
+      s *= 2.0 / vn;
+      for (int j = k + 1; j < n; ++j) Hm[(size_t)i * n + j] -= s * v[j];
+      double s2 = 0.0;
+      for (int j = k + 1; j < n; ++j) s2 += Qm[(size_t)i * n + j] * v[j];
+      s2 *= 2.0 / vn;
+      for (int j = k + 1; j < n; ++j) Qm[(size_t)i * n + j] -= s2 * v[j];
+    }
+    for (int i = k + 2; i < n; ++i) Hm[(size_t)i * n + k] = 0.0;
+  }
+  std::vector<cplx> Hc(Hm.begin(), Hm.end()), Zc(Qm.begin(), Qm.end());
+  if (!complex_schur(n, Hc, Zc)) return false;
+  // Eigenvectors of the triangular factor by back substitution, then Z y.
+  double tnorm = 0.0;
+  for (auto& x : Hc) tnorm = std::max(tnorm, std::abs(x));
+  std::vector<cplx> lam(n), Vall((size_t)n * n);
+  std::vector<cplx> y(n);
+  for (int k = 0; k < n; ++k) {
+    lam[k] = Hc[(size_t)k * n + k];
+    std::fill(y.begin(), y.end(), cplx(0.0));
+    y[k] = 1.0;
+    for (int j = k - 1; j >= 0; --j) {
+      cplx s = 0.0;
+      for (int l = j + 1; l <= k; ++l) s += Hc[(size_t)j * n + l] * y[l];
+      cplx den = Hc[(size_t)j * n + j] - lam[k];
+      if (std::abs(den) < 1e-14 * tnorm) den = 1e-14 * tnorm;
+      y[j] = -s / den;
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) {
+      cplx s = 0.0;
+      for (int l = 0; l <= k; ++l) s += Zc[(size_t)i * n + l] * y[l];
+      Vall[(size_t)i * n + k] = s;
+      nrm += std::norm(s);
+    }
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < n; ++i) Vall[(size_t)i * n + k] /= nrm;
+  }
+  // Classify: real eigenvalues and one member (Im > 0) of each conjugate pair.
+  std::vector<int> keep_real, keep_pos;
+  int n_neg = 0;
+  for (int k = 0; k < n; ++k) {
+    const double thr = 1e-9 * std::max(1.0, std::abs(lam[k]));
+    if (std::fabs(lam[k].imag()) <= thr) keep_real.push_back(k);
+    else if (lam[k].imag() > 0) keep_pos.push_back(k);
+    else ++n_neg;
+  }
+  if ((int)keep_pos.size() != n_neg) return false;
+  std::vector<int> order = keep_real;
+  order.insert(order.end(), keep_pos.begin(), keep_pos.end());
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return lam[a].real() < lam[b].real(); });
+  // Full eigenvector matrix: kept columns, each complex one followed by its conjugate.
+  std::vector<cplx> Vf((size_t)n * n);
+  std::vector<int> col_of(order.size());
+  int c = 0;
+  out.nt = n;
+  out.nsel = (int)order.size();
+  out.lam.clear();
+  out.weight.clear();
+  for (size_t q = 0; q < order.size(); ++q) {
+    const int k = order[q];
+    const bool is_real = std::fabs(lam[k].imag()) <= 1e-9 * std::max(1.0, std::abs(lam[k]));
+    std::vector<cplx> col(n);
+    for (int i = 0; i < n; ++i) col[i] = Vall[(size_t)i * n + k];
+    if (is_real) {
+      int imax = 0;
+      for (int i = 1; i < n; ++i) if (std::abs(col[i]) > std::abs(col[imax])) imax = i;
+      const cplx ph = std::abs(col[imax]) > 0 ? col[imax] / std::abs(col[imax]) : cplx(1.0);
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) {
+        col[i] = cplx((col[i] / ph).real(), 0.0);
+        nrm += std::norm(col[i]);
+      }
+      nrm = std::sqrt(nrm);
+      for (int i = 0; i < n; ++i) col[i] /= nrm;
+      out.lam.push_back(cplx(lam[k].real(), 0.0));
+      out.weight.push_back(1.0);
+    } else {
+      out.lam.push_back(lam[k]);
+      out.weight.push_back(2.0);
+    }
+    col_of[q] = c;
+    for (int i = 0; i < n; ++i) Vf[(size_t)i * n + c] = col[i];
+    ++c;
+    if (!is_real) {
+      for (int i = 0; i < n; ++i) Vf[(size_t)i * n + c] = std::conj(col[i]);
+      ++c;
+    }
+  }
+  if (c != n) return false;
+  std::vector<cplx> Vinv;
+  if (!lu_inverse_cplx(n, Vf, Vinv)) return false;
+  std::vector<double> Binv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Binv[(size_t)i * n + i] = 1.0;
+  if (!lu_solve_real(n, tl.B, Binv, n)) return false;
+  out.V.assign((size_t)n * out.nsel, cplx(0.0));
+  out.W.assign((size_t)out.nsel * n, cplx(0.0));
+  for (int q = 0; q < out.nsel; ++q) {
+    const int cq = col_of[q];
+    for (int i = 0; i < n; ++i) out.V[(size_t)i * out.nsel + q] = Vf[(size_t)i * n + cq];
+    for (int j = 0; j < n; ++j) {
+      cplx s = 0.0;
+      for (int l = 0; l < n; ++l) s += Vinv[(size_t)cq * n + l] * Binv[(size_t)l * n + j];
+      out.W[(size_t)q * n + j] = s;
+    }
+  }
+  // Diagnostics: 1-norm condition estimate and eigen-residual of the full V.
+  double n1 = 0.0, n1i = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0, si = 0.0;
+    for (int i = 0; i < n; ++i) {
+      s += std::abs(Vf[(size_t)i * n + j]);
+      si += std::abs(Vinv[(size_t)i * n + j]);
+    }
+    n1 = std::max(n1, s);
+    n1i = std::max(n1i, si);
+  }
+  out.cond_est = n1 * n1i;
+  double rr = 0.0, cn = 0.0, vn = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cn += C[(size_t)i * n + j] * C[(size_t)i * n + j];
+      vn += std::norm(Vf[(size_t)i * n + j]);
+    }
+  std::vector<cplx> lamf(n);
+  {
+    int cc = 0;
+    for (int q = 0; q < out.nsel; ++q) {
+      lamf[cc++] = out.lam[q];
+      if (out.weight[q] > 1.5) lamf[cc++] = std::conj(out.lam[q]);
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cplx s = 0.0;
+      for (int l = 0; l < n; ++l) s += C[(size_t)i * n + l] * Vf[(size_t)l * n + j];
+      s -= Vf[(size_t)i * n + j] * lamf[j];
+      rr += std::norm(s);
+    }
+  out.resid = std::sqrt(rr) / (std::sqrt(cn) * std::sqrt(vn));
+  return true;
+}
+
+bool sym_gen_eig(int n, const std::vector<double>& K, const std::vector<double>& M,
+                 std::vector<double>& mu, std::vector<double>& Phi) {
+  // Cholesky M = L L^T, C = L^{-1} K L^{-T}, cyclic Jacobi rotations on C,
+  // Phi = L^{-T} Q so that Phi^T M Phi = I and Phi^T K Phi = diag(mu).
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (s <= 0) return false;
+    const double d = std::sqrt(s);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / d;
+    }
+  }
+  // X = L^{-1} K (forward substitution on each column), C = X L^{-T} = (L^{-1} X^T)^T.
+  std::vector<double> X = K;
+  auto fwd = [&](std::vector<double>& Y) {
+    for (int c = 0; c < n; ++c)
+      for (int i = 0; i < n; ++i) {
+        double s = Y[(size_t)i * n + c];
+        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * Y[(size_t)k * n + c];
+        Y[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+      }
+  };
+  fwd(X);
+  std::vector<double> Xt((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Xt[(size_t)i * n + j] = X[(size_t)j * n + i];
+  fwd(Xt);
+  std::vector<double> Cm((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Cm[(size_t)i * n + j] = 0.5 * (Xt[(size_t)i * n + j] + Xt[(size_t)j * n + i]);
+  std::vector<double> Qm((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qm[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = Cm[(size_t)i * n + j] * Cm[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = Cm[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = Cm[(size_t)p * n + p], aqq = Cm[(size_t)q * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = Cm[(size_t)k * n + p], akq = Cm[(size_t)k * n + q];
+          Cm[(size_t)k * n + p] = c * akp - s * akq;
+          Cm[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = Cm[(size_t)p * n + k], aqk = Cm[(size_t)q * n + k];
+          Cm[(size_t)p * n + k] = c * apk - s * aqk;
+          Cm[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double qkp = Qm[(size_t)k * n + p], qkq = Qm[(size_t)k * n + q];
+          Qm[(size_t)k * n + p] = c * qkp - s * qkq;
+          Qm[(size_t)k * n + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  mu.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) mu[i] = Cm[(size_t)i * n + i];
+  // Phi = L^{-T} Q (back substitution with L^T on each column).
+  Phi = Qm;
+  for (int c = 0; c < n; ++c)
+    for (int i = n - 1; i >= 0; --i) {
+      double s = Phi[(size_t)i * n + c];
+      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * Phi[(size_t)k * n + c];
+      Phi[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+    }
+  return true;
+}
+
+bool band_lu(int n, int kl, int ku, std::vector<double>& ab, std::vector<int>& piv) {
+  const int kv = kl + ku, ld = 2 * kl + ku + 1;
+  auto a = [&](int i, int j) -> double& { return ab[(size_t)(kv + i - j) + (size_t)j * ld]; };
+  piv.assign(n, 0);
+  int ju = 0;
+  for (int j = 0; j < n; ++j) {
+    const int km = std::min(kl, n - 1 - j);
+    int p = j;
+    for (int i = j + 1; i <= j + km; ++i)
+      if (std::fabs(a(i, j)) > std::fabs(a(p, j))) p = i;
+    piv[j] = p;
+    if (a(p, j) == 0.0) return false;
+    ju = std::max(ju, std::min(j + ku + (p - j), n - 1));
+    if (p != j)
+      for (int c = j; c <= ju; ++c) std::swap(a(p, c), a(j, c));
+    if (km > 0) {
+      const double inv = 1.0 / a(j, j);
+      for (int i = j + 1; i <= j + km; ++i) a(i, j) *= inv;
+      for (int c = j + 1; c <= ju; ++c) {
+        const double ajc = a(j, c);
+        if (ajc == 0.0) continue;
+        for (int i = j + 1; i <= j + km; ++i) a(i, c) -= a(i, j) * ajc;
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace st

@@ -1,0 +1,955 @@
+// CUDA kernels of the space-time sparse-grid wave solver (sm_103a).
+//
+// Every kernel works on the uniform Q1 grids of one spatial level (see Geo
+// in common.cuh).  Complex vectors of the time eigenbasis are stored
+// mode-major: element (q, a) at q * stride + a.
+#include <atomic>
+#include <cstdio>
+
+#include "bspline.h"
+#include "kernels.h"
+
+namespace st {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kRedBlocks = 304;  // two CTAs per SM for the reduction passes
+
+inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
+
+std::atomic<int64_t> g_launches{0};
+inline void count(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+template <int D> __device__ __forceinline__ void decode(int64_t a, int n, int i[3]) {
+  i[0] = (int)(a % n);
+  if (D > 1) i[1] = (int)((a / n) % n);
+  if (D > 2) i[2] = (int)(a / ((int64_t)n * n));
+}
+
+// Sums of c^2 over the cells shared by a node and each of its 3^D neighbours.
+// The 2^D cells around interior node i are i + e, e in {0,1}^D (cell
+// coordinates); neighbour delta shares cell e iff, per direction, delta = +1
+// needs e = 1, delta = -1 needs e = 0 and delta = 0 takes both.
+template <int D, typename R>
+__device__ __forceinline__ void cell_sums(const R* __restrict__ c2, int N, const int i[3], R* S) {
+  constexpr int NC = 1 << D, NS = ipow3(D);
+  R c[NC];
+#pragma unroll
+  for (int e = 0; e < NC; ++e) {
+    int64_t idx = 0, stride = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      idx += (int64_t)(i[k] + ((e >> k) & 1)) * stride;
+      stride *= N;
+    }
+    c[e] = __ldg(c2 + idx);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    R acc = R(0);
+#pragma unroll
+    for (int e = 0; e < NC; ++e) {
+      bool ok = true;
+      int ss = s;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int dk = ss % 3 - 1;
+        ss /= 3;
+        const int ek = (e >> k) & 1;
+        ok = ok && (dk == 0 || (dk == 1 && ek == 1) || (dk == -1 && ek == 0));
+      }
+      if (ok) acc += c[e];
+    }
+    S[s] = acc;
+  }
+}
+
+template <int D> __device__ __forceinline__ bool neighbour(const int i[3], int s, int n, int64_t& off) {
+  off = 0;
+  int64_t stride = 1;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int dk = s % 3 - 1;
+    s /= 3;
+    const int j = i[k] + dk;
+    ok = ok && (j >= 0) && (j < n);
+    off += (int64_t)dk * stride;
+    stride *= n;
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------------ stencils
+template <int D, typename R, int OP>
+__global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const R* __restrict__ c2,
+                                                    const cx<R>* __restrict__ x, const cx<R>* __restrict__ b,
+                                                    cx<R>* __restrict__ y, const cx<R>* __restrict__ lam,
+                                                    const CocgScal* __restrict__ scal, int64_t stride, R omega) {
+  const int q = blockIdx.y;
+  if (scal != nullptr && !scal[q].active) return;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  constexpr int NS = ipow3(D), CEN = (NS - 1) / 2;
+  int i[3] = {0, 0, 0};
+  decode<D>(a, g.n, i);
+  R S[NS];
+  cell_sums<D, R>(c2, g.N, i, S);
+  const cx<R> l = lam[q];
+  const cx<R> diag = fma_s(R(sc.mtot[CEN]), l, mk<R>(S[CEN] * R(sc.ke[CEN]), R(0)));
+  const int64_t base = (int64_t)q * stride;
+  if (OP == OP_JACOBI_ZERO) {
+    y[base + a] = omega * cdiv(b[base + a], diag);
+    return;
+  }
+  cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int64_t off;
+    if (neighbour<D>(i, s, g.n, off)) {
+      const cx<R> v = x[base + a + off];
+      ak = fma_s(S[s] * R(sc.ke[s]), v, ak);
+      am = fma_s(R(sc.mtot[s]), v, am);
+    }
+  }
+  const cx<R> Ax = fma_c(l, am, ak);
+  if (OP == OP_APPLY) {
+    y[base + a] = Ax;
+  } else if (OP == OP_RESID) {
+    y[base + a] = b[base + a] - Ax;
+  } else {  // OP_JACOBI
+    const cx<R> xo = x[base + a];
+    y[base + a] = xo + omega * cdiv(b[base + a] - Ax, diag);
+  }
+}
+
+template <int D, typename R>
+void stencil_dispatch(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                      cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
+                      cudaStream_t s) {
+  dim3 grid(blocks_for(g.nnodes), nmodes);
+  const R om = (R)omega;
+  switch (op) {
+    case OP_APPLY: k_stencil<D, R, OP_APPLY><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
+    case OP_RESID: k_stencil<D, R, OP_RESID><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
+    case OP_JACOBI: k_stencil<D, R, OP_JACOBI><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
+    default: k_stencil<D, R, OP_JACOBI_ZERO><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
+  }
+}
+
+// --------------------------------------------------------- multigrid transfer
+// Restriction = transpose of Q1 prolongation: coarse interior node I sits at
+// fine interior 2I+1; neighbours at offset delta weigh prod_k (delta_k ? 1/2 : 1).
+template <int D, typename R>
+__global__ void __launch_bounds__(kBlock) k_restrict(Geo gf, Geo gc, const cx<R>* __restrict__ rf,
+                                                     cx<R>* __restrict__ bc, const CocgScal* __restrict__ scal,
+                                                     int64_t sf, int64_t scs) {
+  const int q = blockIdx.y;
+  if (scal != nullptr && !scal[q].active) return;
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= gc.nnodes) return;
+  int ic[3] = {0, 0, 0};
+  decode<D>(I, gc.n, ic);
+  constexpr int NS = ipow3(D);
+  cx<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int ss = s;
+    int64_t idx = 0, stride = 1;
+    R w = R(1);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int dk = ss % 3 - 1;
+      ss /= 3;
+      idx += (int64_t)(2 * ic[k] + 1 + dk) * stride;
+      stride *= gf.n;
+      if (dk != 0) w *= R(0.5);
+    }
+    acc = fma_s(w, rf[(int64_t)q * sf + idx], acc);
+  }
+  bc[(int64_t)q * scs + I] = acc;
+}
+
+// x_f += P x_c: fine grid node g (= interior + 1) takes, per direction, the
+// coarse node g/2 (g even) or the two coarse nodes (g -+ 1)/2 with weight 1/2.
+template <int D, typename R>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, const cx<R>* __restrict__ xc,
+                                                        cx<R>* __restrict__ xf, const CocgScal* __restrict__ scal,
+                                                        int64_t sf, int64_t scs) {
+  const int q = blockIdx.y;
+  if (scal != nullptr && !scal[q].active) return;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= gf.nnodes) return;
+  int i[3] = {0, 0, 0};
+  decode<D>(a, gf.n, i);
+  cx<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int e = 0; e < (1 << D); ++e) {
+    bool ok = true;
+    R w = R(1);
+    int64_t idx = 0, stride = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int gk = i[k] + 1;
+      const int bit = (e >> k) & 1;
+      int G;
+      if ((gk & 1) == 0) {
+        ok = ok && (bit == 0);
+        G = gk >> 1;
+      } else {
+        G = (gk - 1) / 2 + bit;
+        w *= R(0.5);
+      }
+      const int I = G - 1;
+      ok = ok && (I >= 0) && (I < gc.n);
+      idx += (int64_t)I * stride;
+      stride *= gc.n;
+    }
+    if (ok) acc = fma_s(w, xc[(int64_t)q * scs + idx], acc);
+  }
+  xf[(int64_t)q * sf + a] = xf[(int64_t)q * sf + a] + acc;
+}
+
+// ------------------------------------------------------------ band LDL^T
+template <typename R>
+__global__ void k_band_form(const double* __restrict__ Kb, const double* __restrict__ Mb,
+                            const cx<double>* __restrict__ lam, cx<R>* __restrict__ F, int64_t total) {
+  const int q = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const cx<double> l = lam[q];
+  F[(int64_t)q * total + e] = mk<R>((R)(Kb[e] + l.re * Mb[e]), (R)(l.im * Mb[e]));
+}
+
+// Right-looking LDL^T without pivoting of a complex-symmetric band matrix
+// (symmetric part of -i(K + lam M) is Im(lam) M, positive definite when
+// Im lam > 0, and K + lam M is SPD for real lam > 0, so every leading minor is
+// non-singular).  Column k: d_k = a_kk; a_{k+i,k+j} -= a_{k+i,k} a_{k+j,k} / d_k;
+// l_{k+i,k} = a_{k+i,k} / d_k.  One CTA per mode.
+template <typename R>
+__global__ void k_band_ldlt(cx<R>* __restrict__ F, int64_t nrow, int bw, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* col = reinterpret_cast<cx<R>*>(smem_raw);
+  const int q = blockIdx.x;
+  const int W = bw + 1;
+  cx<R>* Fq = F + (int64_t)q * nrow * W;
+  for (int64_t k = 0; k < nrow; ++k) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < W; t += blockDim.x) col[t] = (k + t < nrow) ? Fq[k * W + t] : mk<R>(0, 0);
+    __syncthreads();
+    const cx<R> d = col[0];
+    if (!(d.re * d.re + d.im * d.im > R(0))) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      return;
+    }
+    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
+    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
+    for (int p = threadIdx.x; p < m * m; p += blockDim.x) {
+      const int ii = p / m + 1, jj = p % m + 1;
+      if (jj > ii) continue;
+      cx<R>& tgt = Fq[(k + jj) * W + (ii - jj)];
+      tgt = tgt - (col[ii] * col[jj]) * dinv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x + 1; t <= m; t += blockDim.x) Fq[k * W + t] = col[t] * dinv;
+  }
+}
+
+// x = (L D L^T)^{-1} b for one mode per CTA; the whole vector lives in shared memory.
+template <typename R>
+__global__ void k_band_solve(const cx<R>* __restrict__ F, int64_t nrow, int bw, const cx<R>* __restrict__ b,
+                             cx<R>* __restrict__ x, const CocgScal* __restrict__ scal, int64_t stride) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* v = reinterpret_cast<cx<R>*>(smem_raw);
+  const int q = blockIdx.x;
+  if (scal != nullptr && !scal[q].active) return;
+  const int W = bw + 1;
+  const cx<R>* Fq = F + (int64_t)q * nrow * W;
+  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) v[k] = b[(int64_t)q * stride + k];
+  __syncthreads();
+  for (int64_t k = 0; k < nrow; ++k) {
+    const cx<R> yk = v[k];
+    for (int t = threadIdx.x + 1; t <= bw && k + t < nrow; t += blockDim.x) v[k + t] = v[k + t] - Fq[k * W + t] * yk;
+    __syncthreads();
+  }
+  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) v[k] = cdiv(v[k], Fq[k * W]);
+  __syncthreads();
+  for (int64_t k = nrow - 1; k >= 0; --k) {
+    const cx<R> xk = v[k];
+    for (int t = threadIdx.x + 1; t <= bw && k - t >= 0; t += blockDim.x)
+      v[k - t] = v[k - t] - Fq[(k - t) * W + t] * xk;
+    __syncthreads();
+  }
+  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) x[(int64_t)q * stride + k] = v[k];
+}
+
+// ------------------------------------------------------------ COCG pieces
+enum { RED_BB = 0, RED_ALPHA = 1, RED_RR = 2, RED_BETA = 3, RED_RHO0 = 4 };
+
+template <typename R> __device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of a complex value; thread 0 receives it.
+template <typename R> __device__ __forceinline__ cx<R> block_sum(cx<R> v) {
+  __shared__ R sre[32], sim[32];
+  v.re = warp_sum(v.re);
+  v.im = warp_sum(v.im);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sre[wid] = v.re;
+    sim[wid] = v.im;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  cx<R> r = mk<R>(0, 0);
+  if (wid == 0) {
+    r.re = lane < nw ? sre[lane] : R(0);
+    r.im = lane < nw ? sim[lane] : R(0);
+    r.re = warp_sum(r.re);
+    r.im = warp_sum(r.im);
+  }
+  return r;
+}
+
+// which = 0: bilinear sum a_i b_i ; which = 1: sum |a_i|^2 (real part).
+template <typename R, int WHICH>
+__global__ void __launch_bounds__(kBlock) k_reduce_partial(const cx<R>* __restrict__ a, const cx<R>* __restrict__ b,
+                                                           const CocgScal* __restrict__ scal, double* __restrict__ part,
+                                                           int64_t n, int64_t stride) {
+  const int q = blockIdx.y;
+  if (scal != nullptr && !scal[q].active) return;
+  cx<R> acc = mk<R>(0, 0);
+  const cx<R>* aq = a + (int64_t)q * stride;
+  const cx<R>* bq = b + (int64_t)q * stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const cx<R> u = aq[i];
+    if (WHICH == 0) {
+      acc = fma_c(u, bq[i], acc);
+    } else {
+      acc.re = fma(u.re, u.re, fma(u.im, u.im, acc.re));
+    }
+  }
+  const cx<R> s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    part[((int64_t)q * gridDim.x + blockIdx.x) * 2 + 0] = (double)s.re;
+    part[((int64_t)q * gridDim.x + blockIdx.x) * 2 + 1] = (double)s.im;
+  }
+}
+
+template <int WHICH>
+__global__ void k_reduce_final(CocgScal* __restrict__ scal, const double* __restrict__ part, int nblk, double tol,
+                               int max_iter) {
+  const int q = blockIdx.x;
+  CocgScal& S = scal[q];
+  if (WHICH != RED_BB && !S.active) return;
+  cx<double> acc = mk<double>(0, 0);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    acc.re += part[((int64_t)q * nblk + i) * 2 + 0];
+    acc.im += part[((int64_t)q * nblk + i) * 2 + 1];
+  }
+  const cx<double> v = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  const bool finite = isfinite(v.re) && isfinite(v.im);
+  if (WHICH == RED_BB) {
+    S.bb = v.re;
+    S.rr = v.re;
+    S.iters = 0;
+    S.status = 0;
+    S.active = (v.re > 0.0) ? 1 : 0;
+    if (!finite) {
+      S.status = 7;
+      S.active = 0;
+    }
+  } else if (WHICH == RED_RHO0) {
+    S.rho_re = v.re;
+    S.rho_im = v.im;
+  } else if (WHICH == RED_ALPHA) {
+    const double den = v.re * v.re + v.im * v.im;
+    if (!(den > 0.0) || !finite) {
+      S.status = 7;
+      S.active = 0;
+      return;
+    }
+    // alpha = rho / (p . w)
+    S.alpha_re = (S.rho_re * v.re + S.rho_im * v.im) / den;
+    S.alpha_im = (S.rho_im * v.re - S.rho_re * v.im) / den;
+  } else if (WHICH == RED_RR) {
+    S.rr = v.re;
+    S.iters += 1;
+    if (!finite) {
+      S.status = 7;
+      S.active = 0;
+    } else if (v.re <= tol * tol * S.bb) {
+      S.active = 0;
+    } else if (S.iters >= max_iter) {
+      S.status = 4;
+      S.active = 0;
+    }
+  } else if (WHICH == RED_BETA) {
+    const double den = S.rho_re * S.rho_re + S.rho_im * S.rho_im;
+    if (!(den > 0.0) || !finite) {
+      S.status = 7;
+      S.active = 0;
+      return;
+    }
+    S.beta_re = (v.re * S.rho_re + v.im * S.rho_im) / den;
+    S.beta_im = (v.im * S.rho_re - v.re * S.rho_im) / den;
+    S.rho_re = v.re;
+    S.rho_im = v.im;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_cocg_init(const cx<R>* __restrict__ b, cx<R>* __restrict__ x,
+                                                      cx<R>* __restrict__ r, int64_t n, int64_t stride) {
+  const int q = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = (int64_t)q * stride + i;
+  x[e] = mk<R>(0, 0);
+  r[e] = b[e];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_update_xr(cx<R>* __restrict__ x, cx<R>* __restrict__ r,
+                                                      const cx<R>* __restrict__ p, const cx<R>* __restrict__ w,
+                                                      const CocgScal* __restrict__ scal, double* __restrict__ part,
+                                                      int64_t n, int64_t stride) {
+  const int q = blockIdx.y;
+  if (!scal[q].active) return;
+  const cx<R> al = mk<R>((R)scal[q].alpha_re, (R)scal[q].alpha_im);
+  const cx<R> nal = mk<R>(-al.re, -al.im);
+  cx<R> acc = mk<R>(0, 0);
+  const int64_t base = (int64_t)q * stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[base + i] = fma_c(al, p[base + i], x[base + i]);
+    const cx<R> rn = fma_c(nal, w[base + i], r[base + i]);
+    r[base + i] = rn;
+    acc.re = fma(rn.re, rn.re, fma(rn.im, rn.im, acc.re));
+  }
+  const cx<R> s = block_sum(acc);
+  if (threadIdx.x == 0) {
+    part[((int64_t)q * gridDim.x + blockIdx.x) * 2 + 0] = (double)s.re;
+    part[((int64_t)q * gridDim.x + blockIdx.x) * 2 + 1] = 0.0;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_update_p(cx<R>* __restrict__ p, const cx<R>* __restrict__ z,
+                                                     const CocgScal* __restrict__ scal, int64_t n, int64_t stride,
+                                                     int first) {
+  const int q = blockIdx.y;
+  if (!scal[q].active) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e = (int64_t)q * stride + i;
+  if (first) {
+    p[e] = z[e];
+  } else {
+    const cx<R> be = mk<R>((R)scal[q].beta_re, (R)scal[q].beta_im);
+    p[e] = fma_c(be, p[e], z[e]);
+  }
+}
+
+__global__ void k_activate(CocgScal* scal, int nmodes) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nmodes) scal[q].active = 1;
+}
+
+// --------------------------------------------------------- time transforms
+constexpr int kQB = 4;
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_fwd_transform(const cx<double>* __restrict__ W,
+                                                          const double* __restrict__ Rt, cx<R>* __restrict__ G,
+                                                          int nsel, int nt, int64_t nx) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  const int q0 = blockIdx.y * kQB;
+  cx<double> acc[kQB];
+#pragma unroll
+  for (int u = 0; u < kQB; ++u) acc[u] = mk<double>(0, 0);
+  for (int i = 0; i < nt; ++i) {
+    const double r = Rt[(int64_t)i * nx + a];
+#pragma unroll
+    for (int u = 0; u < kQB; ++u)
+      if (q0 + u < nsel) acc[u] = fma_s(r, W[(int64_t)(q0 + u) * nt + i], acc[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < kQB; ++u)
+    if (q0 + u < nsel) G[(int64_t)(q0 + u) * nx + a] = mk<R>((R)acc[u].re, (R)acc[u].im);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_back_transform(const cx<double>* __restrict__ V,
+                                                           const double* __restrict__ wq,
+                                                           const cx<R>* __restrict__ X, double* __restrict__ U,
+                                                           int nsel, int nt, int64_t nx) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  const int i0 = blockIdx.y * kQB;
+  double acc[kQB];
+#pragma unroll
+  for (int u = 0; u < kQB; ++u) acc[u] = 0.0;
+  for (int q = 0; q < nsel; ++q) {
+    const cx<R> xr = X[(int64_t)q * nx + a];
+    const double xre = (double)xr.re, xim = (double)xr.im, w = wq[q];
+#pragma unroll
+    for (int u = 0; u < kQB; ++u)
+      if (i0 + u < nt) {
+        const cx<double> v = V[(int64_t)(i0 + u) * nsel + q];
+        acc[u] = fma(w, v.re * xre - v.im * xim, acc[u]);
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < kQB; ++u)
+    if (i0 + u < nt) U[(int64_t)(i0 + u) * nx + a] += acc[u];
+}
+
+// ------------------------------------------------------- FP64 residual, loads
+template <int D, bool ALLNODES>
+__global__ void __launch_bounds__(kBlock) k_stencil_real2(Geo g, StencilCoef sc, const double* __restrict__ c2,
+                                                          const double* __restrict__ x, double* __restrict__ K_out,
+                                                          double* __restrict__ M_out, double alphaK, double alphaM,
+                                                          int64_t xrow, int64_t orow, int accumulate) {
+  const int row = blockIdx.y;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  constexpr int NS = ipow3(D);
+  int i[3] = {0, 0, 0};
+  decode<D>(a, g.n, i);
+  double S[NS];
+  cell_sums<D, double>(c2, g.N, i, S);
+  const double* xr = x + (int64_t)row * xrow;
+  double ak = 0.0, am = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double v;
+    if (ALLNODES) {
+      // all (N+1)^D nodes; interior node i sits at grid node i + 1
+      int ss = s;
+      int64_t idx = 0, stride = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int dk = ss % 3 - 1;
+        ss /= 3;
+        idx += (int64_t)(i[k] + 1 + dk) * stride;
+        stride *= (g.N + 1);
+      }
+      v = xr[idx];
+    } else {
+      int64_t off;
+      if (!neighbour<D>(i, s, g.n, off)) continue;
+      v = xr[a + off];
+    }
+    ak = fma(S[s] * sc.ke[s], v, ak);
+    am = fma(sc.mtot[s], v, am);
+  }
+  if (ALLNODES) {
+    const double v = alphaK * ak + alphaM * am;
+    K_out[(int64_t)row * orow + a] = accumulate ? K_out[(int64_t)row * orow + a] + v : v;
+  } else {
+    K_out[(int64_t)row * orow + a] = ak;
+    M_out[(int64_t)row * orow + a] = am;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_time_combine(const double* __restrict__ Aband,
+                                                         const double* __restrict__ Bband,
+                                                         const double* __restrict__ F, const double* __restrict__ KU,
+                                                         const double* __restrict__ MU, double* __restrict__ Rout,
+                                                         int nt, int64_t nx) {
+  const int i = blockIdx.y;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  double acc = F[(int64_t)i * nx + a];
+#pragma unroll
+  for (int t = -2; t <= 2; ++t) {
+    const int j = i + t;
+    if (j < 0 || j >= nt) continue;
+    acc -= Aband[i * 5 + t + 2] * MU[(int64_t)j * nx + a] + Bband[i * 5 + t + 2] * KU[(int64_t)j * nx + a];
+  }
+  Rout[(int64_t)i * nx + a] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_norm2_partial(const double* __restrict__ v, int64_t n,
+                                                          double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(v[i], v[i], acc);
+  const cx<double> s = block_sum(mk<double>(acc, 0.0));
+  if (threadIdx.x == 0) part[blockIdx.x] = s.re;
+}
+
+__global__ void k_norm2_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[i];
+  const cx<double> s = block_sum(mk<double>(acc, 0.0));
+  if (threadIdx.x == 0) out[0] = s.re;
+}
+
+__global__ void __launch_bounds__(kBlock) k_rhs_assemble(const double* __restrict__ coef,
+                                                         const double* __restrict__ L, double* __restrict__ F,
+                                                         int nterm, int nt, int64_t nx) {
+  const int i = blockIdx.y;
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  double acc = 0.0;
+  for (int r = 0; r < nterm; ++r) acc = fma(coef[(int64_t)r * nt + i], L[(int64_t)r * nx + a], acc);
+  F[(int64_t)i * nx + a] = acc;
+}
+
+// ---------------------------------------------------- space eigenbasis method
+constexpr int kTile = 16;
+
+// Y[i][a] (+)= sum_b X[i][b] P[b][a], P = Phi (trans 0) or its transpose stored row-major.
+__global__ void k_gemm_right(const double* __restrict__ X, const double* __restrict__ P, double* __restrict__ Y,
+                             int nt, int64_t nx, int accumulate) {
+  __shared__ double sx[kTile][kTile + 1], sp[kTile][kTile + 1];
+  const int64_t a = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  const int i = blockIdx.y * kTile + threadIdx.y;
+  double acc = 0.0;
+  for (int64_t b0 = 0; b0 < nx; b0 += kTile) {
+    const int64_t bx = b0 + threadIdx.x, by = b0 + threadIdx.y;
+    sx[threadIdx.y][threadIdx.x] = (i < nt && bx < nx) ? X[(int64_t)i * nx + bx] : 0.0;
+    sp[threadIdx.y][threadIdx.x] = (by < nx && a < nx) ? P[by * nx + a] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTile; ++k) acc = fma(sx[threadIdx.y][k], sp[k][threadIdx.x], acc);
+    __syncthreads();
+  }
+  if (i < nt && a < nx) {
+    if (accumulate) Y[(int64_t)i * nx + a] += acc;
+    else Y[(int64_t)i * nx + a] = acc;
+  }
+}
+
+// Banded LU solve with partial pivoting (factor layout of band_lu, spatial
+// mode fastest), one thread per spatial mode, Y column a (stride nx) in place.
+__global__ void k_time_band_solve(const double* __restrict__ ab, const int* __restrict__ piv, double* __restrict__ Y,
+                                  int nt, int64_t nx, int kl, int ku) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  const int kv = kl + ku, ld = 2 * kl + ku + 1;
+  auto A = [&](int i, int j) -> double { return ab[((int64_t)(kv + i - j) + (int64_t)j * ld) * nx + a]; };
+  for (int j = 0; j < nt; ++j) {
+    const int p = piv[(int64_t)j * nx + a];
+    double yj = Y[(int64_t)p * nx + a];
+    if (p != j) {
+      Y[(int64_t)p * nx + a] = Y[(int64_t)j * nx + a];
+      Y[(int64_t)j * nx + a] = yj;
+    }
+    const int km = min(kl, nt - 1 - j);
+    for (int i = j + 1; i <= j + km; ++i) Y[(int64_t)i * nx + a] -= A(i, j) * yj;
+  }
+  for (int j = nt - 1; j >= 0; --j) {
+    const double yj = Y[(int64_t)j * nx + a] / A(j, j);
+    Y[(int64_t)j * nx + a] = yj;
+    for (int i = max(0, j - kv); i < j; ++i) Y[(int64_t)i * nx + a] -= A(i, j) * yj;
+  }
+}
+
+// --------------------------------------------------------------- combination
+// Hierarchical evaluation of Eq. (19) on a nodal target grid.  The Q1 spaces
+// are nested, so a component of spatial level j < j* evaluated at the target
+// nodes equals its bilinear prolongation through the levels j+1..j*.
+// Level by level, Y_j = P Y_{j-1} + sum_{components at level j} c_k u_k(., t_s),
+// on all nodes of level j (boundary included, for the lift by u0); a component
+// finer than the target level is injected (its nodes contain the target nodes).
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __restrict__ Yprev,
+                                                       const CombComp* __restrict__ comps, int c0, int c1,
+                                                       const double* __restrict__ tbv, const int* __restrict__ tspan,
+                                                       int nts, double* __restrict__ Y) {
+  const int s = blockIdx.y;
+  const int Nj = 1 << j;
+  int64_t nsp = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) nsp *= (Nj + 1);
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nsp) return;
+  int P[3] = {0, 0, 0};
+  {
+    int64_t r = p;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      P[k] = (int)(r % (Nj + 1));
+      r /= (Nj + 1);
+    }
+  }
+  double v = 0.0;
+  if (Yprev != nullptr) {
+    // bilinear prolongation from level j-1 (all nodes): per direction the
+    // coarse node P/2 (even P) or (P-1)/2 and (P+1)/2 with weight 1/2
+    const int Nc = Nj >> 1;
+    const double* Ys = Yprev;
+    int64_t ncs = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) ncs *= (Nc + 1);
+    Ys += (int64_t)s * ncs;
+#pragma unroll
+    for (int e = 0; e < (1 << D); ++e) {
+      bool ok = true;
+      double w = 1.0;
+      int64_t idx = 0, st = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int bit = (e >> k) & 1;
+        int G;
+        if ((P[k] & 1) == 0) {
+          ok = ok && (bit == 0);
+          G = P[k] >> 1;
+        } else {
+          G = (P[k] >> 1) + bit;
+          w *= 0.5;
+        }
+        idx += (int64_t)G * st;
+        st *= (Nc + 1);
+      }
+      if (ok) v = fma(w, Ys[idx], v);
+    }
+  }
+  bool interior = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) interior = interior && P[k] >= 1 && P[k] <= Nj - 1;
+  for (int c = c0; c < c1; ++c) {
+    const CombComp cc = comps[c];
+    const int sh = cc.jx - j;  // >= 0: injection from a finer component grid
+    const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
+    double val = 0.0;
+    if (interior) {
+      int64_t ii = 0, si = 1, nx = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ii += (int64_t)((P[k] << sh) - 1) * si;
+        si *= n;
+        nx *= n;
+      }
+      const int span = tspan[(int64_t)c * nts + s];
+      const double* tb = tbv + ((int64_t)c * nts + s) * 3;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int row = span + t - 1;
+        if (row >= 0 && row < nt) val = fma(tb[t], cc.U[(int64_t)row * nx + ii], val);
+      }
+    }
+    if (cc.lift != nullptr) {
+      int64_t ia = 0, sa = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ia += (int64_t)(P[k] << sh) * sa;
+        sa *= (N + 1);
+      }
+      val += cc.lift[ia];
+    }
+    v = fma((double)cc.coef, val, v);
+  }
+  Y[(int64_t)s * nsp + p] = v;
+}
+
+}  // namespace
+
+// ================================================================ wrappers
+template <typename R>
+void launch_stencil(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                    cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
+                    cudaStream_t s) {
+  count(1);
+  if (g.d == 1) stencil_dispatch<1, R>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+  else if (g.d == 2) stencil_dispatch<2, R>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+  else stencil_dispatch<3, R>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+}
+
+template <typename R>
+void launch_restrict(const Geo& gf, const Geo& gc, const cx<R>* rf, cx<R>* bc, const CocgScal* scal, int nmodes,
+                     int64_t sf, int64_t scs, cudaStream_t s) {
+  count(1);
+  dim3 grid(blocks_for(gc.nnodes), nmodes);
+  if (gf.d == 1) k_restrict<1, R><<<grid, kBlock, 0, s>>>(gf, gc, rf, bc, scal, sf, scs);
+  else if (gf.d == 2) k_restrict<2, R><<<grid, kBlock, 0, s>>>(gf, gc, rf, bc, scal, sf, scs);
+  else k_restrict<3, R><<<grid, kBlock, 0, s>>>(gf, gc, rf, bc, scal, sf, scs);
+}
+
+template <typename R>
+void launch_prolong_add(const Geo& gf, const Geo& gc, const cx<R>* xc, cx<R>* xf, const CocgScal* scal, int nmodes,
+                        int64_t sf, int64_t scs, cudaStream_t s) {
+  count(1);
+  dim3 grid(blocks_for(gf.nnodes), nmodes);
+  if (gf.d == 1) k_prolong_add<1, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
+  else if (gf.d == 2) k_prolong_add<2, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
+  else k_prolong_add<3, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
+}
+
+template <typename R>
+void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, int64_t nrow, int bw,
+                      int nmodes, cudaStream_t s) {
+  count(1);
+  const int64_t total = nrow * (bw + 1);
+  k_band_form<R><<<dim3(blocks_for(total), nmodes), kBlock, 0, s>>>(Kb, Mb, lam, F, total);
+}
+
+template <typename R>
+void launch_band_ldlt(cx<R>* F, int64_t nrow, int bw, int nmodes, int* err, cudaStream_t s) {
+  count(1);
+  k_band_ldlt<R><<<nmodes, 256, (bw + 1) * sizeof(cx<R>), s>>>(F, nrow, bw, err);
+}
+
+template <typename R>
+void launch_band_solve(const cx<R>* F, int64_t nrow, int bw, const cx<R>* b, cx<R>* x, const CocgScal* scal,
+                       int nmodes, int64_t stride, cudaStream_t s) {
+  count(1);
+  int threads = ((bw + 31) / 32) * 32;
+  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+  const size_t smem = (size_t)nrow * sizeof(cx<R>);
+  static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once per type
+  if (!attr) {
+    cudaFuncSetAttribute(k_band_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr = true;
+  }
+  k_band_solve<R><<<nmodes, threads, smem, s>>>(F, nrow, bw, b, x, scal, stride);
+}
+
+template <typename R>
+void launch_cocg_init(const cx<R>* b, cx<R>* x, cx<R>* r, CocgScal* scal, double* part, int nmodes, int64_t n,
+                      int64_t stride, cudaStream_t s) {
+  count(3);
+  k_cocg_init<R><<<dim3(blocks_for(n), nmodes), kBlock, 0, s>>>(b, x, r, n, stride);
+  k_reduce_partial<R, 1><<<dim3(kRedBlocks, nmodes), kBlock, 0, s>>>(b, b, nullptr, part, n, stride);
+  k_reduce_final<RED_BB><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, 0.0, 0);
+}
+
+template <typename R>
+void launch_dot(int which, const cx<R>* a, const cx<R>* b, CocgScal* scal, double* part, int nmodes, int64_t n,
+                int64_t stride, double tol, int max_iter, cudaStream_t s) {
+  count(2);
+  k_reduce_partial<R, 0><<<dim3(kRedBlocks, nmodes), kBlock, 0, s>>>(a, b, scal, part, n, stride);
+  if (which == 0) k_reduce_final<RED_ALPHA><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter);
+  else if (which == 1) k_reduce_final<RED_BETA><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter);
+  else k_reduce_final<RED_RHO0><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter);
+}
+
+template <typename R>
+void launch_update_xr(cx<R>* x, cx<R>* r, const cx<R>* p, const cx<R>* w, CocgScal* scal, double* part,
+                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s) {
+  count(2);
+  k_update_xr<R><<<dim3(kRedBlocks, nmodes), kBlock, 0, s>>>(x, r, p, w, scal, part, n, stride);
+  k_reduce_final<RED_RR><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter);
+}
+
+template <typename R>
+void launch_update_p(cx<R>* p, const cx<R>* z, const CocgScal* scal, int nmodes, int64_t n, int64_t stride,
+                     int first, cudaStream_t s) {
+  k_update_p<R><<<dim3(blocks_for(n), nmodes), kBlock, 0, s>>>(p, z, scal, n, stride, first);
+  count(1);
+}
+
+void launch_cocg_activate(CocgScal* scal, int nmodes, cudaStream_t s) {
+  count(1);
+  k_activate<<<(nmodes + 127) / 128, 128, 0, s>>>(scal, nmodes);
+}
+
+template <typename R>
+void launch_fwd_transform(const cx<double>* W, const double* Rt, cx<R>* G, int nsel, int nt, int64_t nx,
+                          cudaStream_t s) {
+  count(1);
+  k_fwd_transform<R><<<dim3(blocks_for(nx), (nsel + kQB - 1) / kQB), kBlock, 0, s>>>(W, Rt, G, nsel, nt, nx);
+}
+
+template <typename R>
+void launch_back_transform(const cx<double>* V, const double* wq, const cx<R>* X, double* U, int nsel, int nt,
+                           int64_t nx, cudaStream_t s) {
+  count(1);
+  k_back_transform<R><<<dim3(blocks_for(nx), (nt + kQB - 1) / kQB), kBlock, 0, s>>>(V, wq, X, U, nsel, nt, nx);
+}
+
+void launch_residual(const Geo& g, const StencilCoef& sc, const double* c2, const double* U, const double* F,
+                     const double* Aband, const double* Bband, double* KU, double* MU, double* Rout, int nt,
+                     cudaStream_t s) {
+  count(2);
+  dim3 grid(blocks_for(g.nnodes), nt);
+  if (g.d == 1) k_stencil_real2<1, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
+  else if (g.d == 2) k_stencil_real2<2, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
+  else k_stencil_real2<3, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
+  k_time_combine<<<grid, kBlock, 0, s>>>(Aband, Bband, F, KU, MU, Rout, nt, g.nnodes);
+}
+
+void launch_norm2(const double* v, int64_t n, double* part, double* out, cudaStream_t s) {
+  count(2);
+  k_norm2_partial<<<kRedBlocks, kBlock, 0, s>>>(v, n, part);
+  k_norm2_final<<<1, 256, 0, s>>>(part, kRedBlocks, out);
+}
+
+void launch_load(const Geo& g, const StencilCoef& sc, const double* c2, const double* xall, double* out,
+                 double alphaK, double alphaM, int accumulate, cudaStream_t s) {
+  count(1);
+  dim3 grid(blocks_for(g.nnodes), 1);
+  if (g.d == 1) k_stencil_real2<1, true><<<grid, kBlock, 0, s>>>(g, sc, c2, xall, out, nullptr, alphaK, alphaM, 0, 0, accumulate);
+  else if (g.d == 2) k_stencil_real2<2, true><<<grid, kBlock, 0, s>>>(g, sc, c2, xall, out, nullptr, alphaK, alphaM, 0, 0, accumulate);
+  else k_stencil_real2<3, true><<<grid, kBlock, 0, s>>>(g, sc, c2, xall, out, nullptr, alphaK, alphaM, 0, 0, accumulate);
+}
+
+void launch_rhs_assemble(const double* coef, const double* L, double* F, int nterm, int nt, int64_t nx,
+                         cudaStream_t s) {
+  count(1);
+  k_rhs_assemble<<<dim3(blocks_for(nx), nt), kBlock, 0, s>>>(coef, L, F, nterm, nt, nx);
+}
+
+void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, int64_t nx, int trans, int accumulate,
+                       cudaStream_t s) {
+  count(1);
+  (void)trans;  // the caller passes Phi or its stored transpose
+  dim3 block(kTile, kTile), grid((unsigned)((nx + kTile - 1) / kTile), (nt + kTile - 1) / kTile);
+  k_gemm_right<<<grid, block, 0, s>>>(X, Phi, Y, nt, nx, accumulate);
+}
+
+void launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
+                            cudaStream_t s) {
+  count(1);
+  k_time_band_solve<<<blocks_for(nx, 128), 128, 0, s>>>(ab, piv, Y, nt, nx, kl, ku);
+}
+
+void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,
+                       const int* tspan, int nts, double* Y, cudaStream_t s) {
+  count(1);
+  int64_t nsp = 1;
+  for (int k = 0; k < d; ++k) nsp *= ((1 << j) + 1);
+  dim3 grid(blocks_for(nsp), nts);
+  if (d == 1) k_comb_level<1><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
+  else if (d == 2) k_comb_level<2><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
+  else k_comb_level<3><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
+}
+
+int64_t kernel_launch_count() { return g_launches.load(); }
+
+// explicit instantiations
+#define ST_INST(R)                                                                                                   \
+  template void launch_stencil<R>(int, const Geo&, const StencilCoef&, const R*, const cx<R>*, const cx<R>*, cx<R>*, \
+                                  const cx<R>*, const CocgScal*, int, int64_t, double, cudaStream_t);                \
+  template void launch_restrict<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,      \
+                                   int64_t, cudaStream_t);                                                           \
+  template void launch_prolong_add<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,   \
+                                      int64_t, cudaStream_t);                                                        \
+  template void launch_band_form<R>(const double*, const double*, const cx<double>*, cx<R>*, int64_t, int, int,      \
+                                    cudaStream_t);                                                                   \
+  template void launch_band_ldlt<R>(cx<R>*, int64_t, int, int, int*, cudaStream_t);                                 \
+  template void launch_band_solve<R>(const cx<R>*, int64_t, int, const cx<R>*, cx<R>*, const CocgScal*, int,         \
+                                     int64_t, cudaStream_t);                                                         \
+  template void launch_cocg_init<R>(const cx<R>*, cx<R>*, cx<R>*, CocgScal*, double*, int, int64_t, int64_t,         \
+                                    cudaStream_t);                                                                   \
+  template void launch_dot<R>(int, const cx<R>*, const cx<R>*, CocgScal*, double*, int, int64_t, int64_t, double,    \
+                              int, cudaStream_t);                                                                    \
+  template void launch_update_xr<R>(cx<R>*, cx<R>*, const cx<R>*, const cx<R>*, CocgScal*, double*, int, int64_t,    \
+                                    int64_t, double, int, cudaStream_t);                                             \
+  template void launch_update_p<R>(cx<R>*, const cx<R>*, const CocgScal*, int, int64_t, int64_t, int, cudaStream_t);      \
+  template void launch_fwd_transform<R>(const cx<double>*, const double*, cx<R>*, int, int, int64_t, cudaStream_t);  \
+  template void launch_back_transform<R>(const cx<double>*, const double*, const cx<R>*, double*, int, int, int64_t, \
+                                         cudaStream_t);
+ST_INST(double)
+ST_INST(float)
+#undef ST_INST
+
+}  // namespace st

@@ -1,0 +1,108 @@
+// Launch wrappers of the space-time solver kernels (kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace st {
+
+enum StencilOp { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_JACOBI_ZERO = 3 };
+
+// Per-mode state of the batched COCG iteration (device memory).
+struct CocgScal {
+  double rho_re, rho_im;     // r . z  (bilinear)
+  double alpha_re, alpha_im;
+  double beta_re, beta_im;
+  double rr, bb;             // ||r||^2, ||b||^2
+  int active, iters, status, pad;
+};
+
+// y_q = op((K(c2) + lam_q M) x_q) for every active mode q of a level.
+template <typename R>
+void launch_stencil(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x,
+                    const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
+                    int64_t stride, double omega, cudaStream_t s);
+
+// Multigrid transfers between level gf (fine) and gc = coarse (N/2).
+template <typename R>
+void launch_restrict(const Geo& gf, const Geo& gc, const cx<R>* rf, cx<R>* bc, const CocgScal* scal, int nmodes,
+                     int64_t sf, int64_t scs, cudaStream_t s);
+template <typename R>
+void launch_prolong_add(const Geo& gf, const Geo& gc, const cx<R>* xc, cx<R>* xf, const CocgScal* scal, int nmodes,
+                        int64_t sf, int64_t scs, cudaStream_t s);
+
+// Banded complex-symmetric LDL^T (lower band b, column storage F[q][k][j] =
+// entry (k+j, k)): form K + lam_q M from the real bands, factorise, solve.
+template <typename R>
+void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, int64_t nrow, int bw,
+                      int nmodes, cudaStream_t s);
+template <typename R>
+void launch_band_ldlt(cx<R>* F, int64_t nrow, int bw, int nmodes, int* err, cudaStream_t s);
+template <typename R>
+void launch_band_solve(const cx<R>* F, int64_t nrow, int bw, const cx<R>* b, cx<R>* x, const CocgScal* scal,
+                       int nmodes, int64_t stride, cudaStream_t s);
+
+// COCG vector steps with deterministic two-pass reductions.
+template <typename R>
+void launch_cocg_init(const cx<R>* b, cx<R>* x, cx<R>* r, CocgScal* scal, double* part, int nmodes, int64_t n,
+                      int64_t stride, cudaStream_t s);
+template <typename R>
+void launch_dot(int which, const cx<R>* a, const cx<R>* b, CocgScal* scal, double* part, int nmodes, int64_t n,
+                int64_t stride, double tol, int max_iter, cudaStream_t s);
+template <typename R>
+void launch_update_xr(cx<R>* x, cx<R>* r, const cx<R>* p, const cx<R>* w, CocgScal* scal, double* part,
+                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s);
+template <typename R>
+void launch_update_p(cx<R>* p, const cx<R>* z, const CocgScal* scal, int nmodes, int64_t n, int64_t stride,
+                     int first, cudaStream_t s);
+void launch_cocg_activate(CocgScal* scal, int nmodes, cudaStream_t s);
+
+// Time transforms of the eigenbasis method (FP64 matrices):
+// G[q][a] = sum_i W[q][i] R[i][a];  U[i][a] += sum_q w_q Re(V[i][q] X[q][a]).
+template <typename R>
+void launch_fwd_transform(const cx<double>* W, const double* Rt, cx<R>* G, int nsel, int nt, int64_t nx,
+                          cudaStream_t s);
+template <typename R>
+void launch_back_transform(const cx<double>* V, const double* wq, const cx<R>* X, double* U, int nsel, int nt,
+                           int64_t nx, cudaStream_t s);
+
+// FP64 space-time residual R = F - (A (x) M + B (x) K) U (banded time factors).
+void launch_residual(const Geo& g, const StencilCoef& sc, const double* c2, const double* U, const double* F,
+                     const double* Aband, const double* Bband, double* KU, double* MU, double* Rout, int nt,
+                     cudaStream_t s);
+// Sum of squares of a real vector (deterministic), result to out[0] (device).
+void launch_norm2(const double* v, int64_t n, double* part, double* out, cudaStream_t s);
+
+// Loads of Q1-interpolated data: out = alphaK K_load x + alphaM M_load x with x on ALL nodes.
+void launch_load(const Geo& g, const StencilCoef& sc, const double* c2, const double* xall, double* out,
+                 double alphaK, double alphaM, int accumulate, cudaStream_t s);
+// F[i][a] = sum_r coef[r][i] L[r][a]  (rank-nterm assembly)
+void launch_rhs_assemble(const double* coef, const double* L, double* F, int nterm, int nt, int64_t nx,
+                         cudaStream_t s);
+
+// Space eigenbasis method: Y = X Phi (trans = 0) or Y = X Phi^T (trans = 1),
+// X nt x nx, Phi nx x nx; then banded time solves per spatial mode.
+void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, int64_t nx, int trans, int accumulate,
+                       cudaStream_t s);
+void launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
+                            cudaStream_t s);
+
+// Combination kernel (Eq. (19)) on a nodal target grid.
+struct CombComp {
+  const double* U;     // nt x nx interior coefficients (FP64)
+  const double* lift;  // u0 on all nodes of level jx, or nullptr
+  int jx, jt, coef, pad;
+};
+// One level of the hierarchical combination: Y = P Yprev + sum over
+// components c0..c1-1 (all at spatial level >= j, listed in comps) of
+// coef * u_k(., t_s) on the (2^j+1)^d nodes of level j, for every target time.
+// tbv[c][s][0..2]: the three B-spline values of component c at target time s,
+// tspan[c][s] their interval.  Yprev (level j-1, all nodes x nts) may be null.
+void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,
+                       const int* tspan, int nts, double* Y, cudaStream_t s);
+
+// Kernels launched by this process through the wrappers above.
+int64_t kernel_launch_count();
+
+}  // namespace st

@@ -1,0 +1,1338 @@
+// C ABI of the space-time sparse-grid wave solver: setup, component solves,
+// combination.  Declarations and contracts: include/st.h.
+//
+// Component solve (Eq. (9) in the form of Eq. (30)):
+//   (A (x) M + B (x) K) vec(U) = vec(F),   U: n_t x N_x, time-major.
+// Time eigenbasis method: with B^{-1} A = V Lam V^{-1} and W = V^{-1} B^{-1},
+//   G = W F,  (lam_q M + K) x_q = g_q for every mode q,  U = V X,
+// conjugate modes folded (U = sum_real V_q x_q + 2 Re sum_pairs V_q x_q).
+// Each spatial problem is complex symmetric; it is solved by COCG with a
+// geometric multigrid V-cycle whose coarsest grid resolves the mode's wave
+// number and is solved by a banded LDL^T, or by the banded LDL^T alone on
+// small grids.
+// Space eigenbasis method (fine time levels): K Phi = M Phi diag(mu),
+// Phi^T M Phi = I, so Y = F Phi, (A + mu_a B) c_a = y_a (banded LU),
+// U = C Phi^T.
+// Both are wrapped in FP64 iterative refinement on R = F - (A (x) M + B (x) K) U.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/st.h"
+#include "../../include/st_host.h"
+#include "host_math.h"
+#include "kernels.h"
+
+using namespace st;
+
+namespace {
+
+constexpr int kMaxDirectRows = 4096;   // banded direct solves keep the vector in shared memory
+constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
+constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
+constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64
+constexpr double kThetaMG = 1.25;      // coarsest-grid resolution: k h_c <= theta
+constexpr double kOmega2D = 0.6, kOmega3D = 0.55, kOmega1D = 0.6;
+
+struct DevMem {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  ~DevMem() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+struct Status {
+  st_status code = ST_OK;
+  std::string msg;
+};
+
+// Stencil coefficient tables of a level (element matrices of Section 3.2:
+// K1 = 1/h [1 -1; -1 1], M1 = h/6 [2 1; 1 2] per direction).
+StencilCoef make_coef(int d, const double* h) {
+  StencilCoef sc;
+  std::memset(&sc, 0, sizeof(sc));
+  const int ns = ipow3(d);
+  for (int s = 0; s < ns; ++s) {
+    int dl[3] = {0, 0, 0};
+    int ss = s, zeros = 0;
+    for (int k = 0; k < d; ++k) {
+      dl[k] = ss % 3 - 1;
+      ss /= 3;
+      if (dl[k] == 0) ++zeros;
+    }
+    auto K1 = [&](int k) { return dl[k] == 0 ? 1.0 / h[k] : -1.0 / h[k]; };
+    auto M1 = [&](int k) { return dl[k] == 0 ? h[k] / 3.0 : h[k] / 6.0; };
+    double ke = 0.0;
+    for (int dir = 0; dir < d; ++dir) {
+      double t = 1.0;
+      for (int k = 0; k < d; ++k) t *= (k == dir) ? K1(k) : M1(k);
+      ke += t;
+    }
+    double m = (double)(1 << zeros);
+    for (int k = 0; k < d; ++k) m *= M1(k);
+    sc.ke[s] = ke;
+    sc.mtot[s] = m;
+  }
+  return sc;
+}
+
+Geo make_geo(int d, int j) {
+  Geo g;
+  g.d = d;
+  g.N = 1 << j;
+  g.n = g.N - 1;
+  g.nnodes = 1;
+  g.ncells = 1;
+  for (int k = 0; k < d; ++k) {
+    g.nnodes *= g.n;
+    g.ncells *= g.N;
+  }
+  return g;
+}
+
+int64_t band_width(const Geo& g) {
+  if (g.d == 1) return 1;
+  if (g.d == 2) return (int64_t)g.n + 1;
+  return (int64_t)g.n * g.n + g.n + 1;
+}
+
+// One spatial multigrid level (c^2 of the component level, or cell averages of it).
+struct MGLevel {
+  int j = 0;
+  Geo geo{};
+  StencilCoef sc{};
+  std::vector<double> c2h;
+  double* c2d = nullptr;
+  float* c2f = nullptr;
+};
+
+struct SpaceLevel {
+  int jx = 0;
+  Geo geo{};
+  double h[3] = {0, 0, 0};
+  StencilCoef sc{};
+  std::vector<double> c2h;  // cellwise c^2 at the cell centres
+  double* c2d = nullptr;
+  float* c2f = nullptr;
+  double* lift = nullptr;   // u0 on all nodes (nullptr if u0 == 0)
+  double* loads = nullptr;  // (nterm + 2) x nx: M g_r ..., M v0, K u0
+  double c2min = 0.0;
+  int64_t nall = 0;
+};
+
+struct TimeData {
+  TimeLevel tl;
+  TimeEig eig;
+  bool have_eig = false;
+  double* Aband = nullptr;  // nt x 5
+  double* Bband = nullptr;
+  cx<double>* W = nullptr;  // nsel x nt
+  cx<double>* V = nullptr;  // nt x nsel
+  double* wq = nullptr;
+  cx<double>* lam64 = nullptr;
+  cx<float>* lam32 = nullptr;
+  double* rhs_coef = nullptr;  // (nterm + 2) x nt
+};
+
+template <typename R> struct Work {
+  // level-0 vectors (nsel x nx): rhs G, iterate X, residual, search P, A P, z, smoother scratch
+  cx<R>* G = nullptr;
+  cx<R>* X = nullptr;
+  cx<R>* Rr = nullptr;
+  cx<R>* P = nullptr;
+  cx<R>* Wv = nullptr;
+  cx<R>* Z = nullptr;
+  cx<R>* T0 = nullptr;
+  cx<R>* R0 = nullptr;
+  std::vector<cx<R>*> bl, rl, xa, xb;  // per MG level l >= 1
+  cx<R>* band = nullptr;               // nsel x nrow x (bw + 1)
+  bool ready = false;
+};
+
+struct Component {
+  int jx = 0, jt = 0, coef = 0;
+  int method = 0;  // 0 = time eigenbasis, 1 = space eigenbasis
+  int64_t nx = 0;
+  int nt = 0;
+  SpaceLevel* sl = nullptr;
+  TimeData* td = nullptr;
+  double* F = nullptr;
+  double* U = nullptr;
+  double* Rv = nullptr;
+  double* KU = nullptr;
+  double* MU = nullptr;
+  double* Fg_all = nullptr;  // general source, time-projected on all nodes (nt x nall), or nullptr
+  bool f_ready = false;
+  bool solved = false;
+  // time eigenbasis
+  int nsel = 0;
+  bool inner64 = false;
+  bool direct = false;
+  int jc = 0;
+  std::vector<MGLevel> mg;  // mg[0] = component level
+  int64_t nrowc = 0;
+  int bw = 0;
+  std::vector<double> Kband, Mband;
+  double* Kb = nullptr;
+  double* Mb = nullptr;
+  Work<double> w64;
+  Work<float> w32;
+  CocgScal* scal = nullptr;
+  double* part = nullptr;
+  std::vector<CocgScal> scal_h;
+  // space eigenbasis
+  double* Phi = nullptr;
+  double* PhiT = nullptr;
+  double* ab = nullptr;
+  int* piv = nullptr;
+  int kl = 2, ku = 2;
+  double Snorm = 0.0;  // upper bound of ||A (x) M + B (x) K||_2
+  st_solve_info info{};
+  int nactive = 0;  // modes still iterating at the last host check (for byte accounting)
+};
+
+// Algorithmic flops per node of the complex Q1 stencil (K and M parts with
+// 3^d neighbours, then the complex shift) and per node-mode for the real one.
+inline double stencil_flops(int d) { return 8.0 * ipow3(d) + 8.0; }
+
+}  // namespace
+
+struct st_handle {
+  st_problem prob{};
+  st_options opt{};
+  cudaStream_t stream = nullptr;
+  DevMem mem;
+  std::map<int, std::unique_ptr<SpaceLevel>> space;
+  std::map<int, std::unique_ptr<TimeData>> time;
+  std::vector<std::unique_ptr<Component>> comps;
+  int nterm_rows = 0;  // n_terms + 2
+  double* part = nullptr;
+  double* scalar = nullptr;
+  double* scalar_h = nullptr;  // pinned
+  int64_t launches0 = 0;
+  std::string err;
+  int* dev_err = nullptr;
+  struct CombTables {
+    CombComp* comps = nullptr;  // components ordered by combination level
+    double* tb = nullptr;
+    int* span = nullptr;
+    int jmin = 0;
+    std::vector<int> first;     // first[lev] = first component of level lev
+    std::vector<double*> Y;     // partial sums of the levels below the target
+  };
+  std::map<std::pair<int, int>, CombTables> comb;  // per target level pair
+
+  // Optional per-kernel-class timing: CUDA events recorded on the handle's
+  // stream around every launch, with the algorithmic bytes and flops of it.
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t get_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+
+  ~st_handle() {
+    if (scalar_h) cudaFreeHost(scalar_h);
+    for (auto& r : prof) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
+
+  template <typename T> T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.ptrs.push_back(p);
+    mem.bytes += n * sizeof(T);
+    return static_cast<T*>(p);
+  }
+  template <typename T> T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>(v.size());
+    if (p && !v.empty()) {
+      cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream);
+      h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    }
+    return p;
+  }
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+st_status fail(st_handle* h, st_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define ST_CUDA(h, call)                                                                    \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(h, ST_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ST_NEED(h, ptr)                                                          \
+  do {                                                                           \
+    if ((ptr) == nullptr) return fail(h, ST_ERR_OOM, "device allocation failed"); \
+  } while (0)
+
+enum KClass {
+  KC_STENCIL = 0, KC_JACOBI, KC_MG_RESID, KC_RESTRICT, KC_PROLONG, KC_BAND_SOLVE, KC_REDUCE, KC_UPDATE,
+  KC_TRANSFORM, KC_RESIDUAL64, KC_NORM, KC_RHS, KC_SPACE_EIG, KC_COMBINE, KC_SETUP, KC_COUNT
+};
+const char* const kClassName[KC_COUNT] = {"stencil_apply", "jacobi_smooth", "mg_residual", "mg_restrict",
+                                          "mg_prolong", "band_solve", "cocg_reduce", "cocg_update",
+                                          "time_transform", "st_residual_fp64", "norm_fp64", "rhs_assemble",
+                                          "space_eigenbasis", "combine_level", "setup"};
+
+struct ProfScope {
+  st_handle* h;
+  int cls;
+  double bytes, flops;
+  cudaEvent_t a = nullptr;
+  ProfScope(st_handle* h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+    if (h->prof_on) {
+      a = h->get_event();
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = h->get_event();
+      cudaEventRecord(b, h->stream);
+      h->prof.push_back({cls, a, b, bytes, flops});
+    }
+  }
+};
+#define PROF(h, cls, bytes, flops, call) \
+  do {                                  \
+    ProfScope ps_(h, cls, bytes, flops); \
+    call;                               \
+  } while (0)
+
+st_status check_launch(st_handle* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, ST_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return ST_OK;
+}
+
+// Evaluate a space callback at points (n x d).
+st_status eval_space(st_handle* h, const st_field& f, const std::vector<double>& pts, int d, std::vector<double>& out) {
+  const int64_t n = (int64_t)pts.size() / d;
+  out.assign(n, 0.0);
+  if (f.fn == nullptr) return ST_OK;
+  if (f.fn(n, pts.data(), out.data(), f.user) != 0) return fail(h, ST_ERR_CALLBACK, "space callback failed");
+  return ST_OK;
+}
+
+std::vector<double> node_points(const st_problem& p, int j) {
+  const int N = 1 << j, d = p.d;
+  int64_t nn = 1;
+  for (int k = 0; k < d; ++k) nn *= (N + 1);
+  std::vector<double> pts((size_t)nn * d);
+  for (int64_t a = 0; a < nn; ++a) {
+    int64_t r = a;
+    for (int k = 0; k < d; ++k) {
+      const int ik = (int)(r % (N + 1));
+      r /= (N + 1);
+      pts[(size_t)a * d + k] = p.lo[k] + (p.hi[k] - p.lo[k]) * ik / N;
+    }
+  }
+  return pts;
+}
+
+std::vector<double> cell_centres(const st_problem& p, int j) {
+  const int N = 1 << j, d = p.d;
+  int64_t nc = 1;
+  for (int k = 0; k < d; ++k) nc *= N;
+  std::vector<double> pts((size_t)nc * d);
+  for (int64_t a = 0; a < nc; ++a) {
+    int64_t r = a;
+    for (int k = 0; k < d; ++k) {
+      const int ik = (int)(r % N);
+      r /= N;
+      pts[(size_t)a * d + k] = p.lo[k] + (p.hi[k] - p.lo[k]) * (ik + 0.5) / N;
+    }
+  }
+  return pts;
+}
+
+// Real band of K(c2) and M of a level: entry (k + j, k) at [k * (bw + 1) + j].
+void assemble_band(const Geo& g, const StencilCoef& sc, const std::vector<double>& c2, std::vector<double>& Kb,
+                   std::vector<double>& Mb, int bw) {
+  const int64_t W = bw + 1;
+  Kb.assign((size_t)(g.nnodes * W), 0.0);
+  Mb.assign((size_t)(g.nnodes * W), 0.0);
+  const int d = g.d, n = g.n, N = g.N;
+  const int ns = ipow3(d);
+  for (int64_t a = 0; a < g.nnodes; ++a) {
+    int i[3] = {0, 0, 0};
+    int64_t r = a;
+    for (int k = 0; k < d; ++k) {
+      i[k] = (int)(r % n);
+      r /= n;
+    }
+    double c[8];
+    for (int e = 0; e < (1 << d); ++e) {
+      int64_t idx = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        idx += (int64_t)(i[k] + ((e >> k) & 1)) * st;
+        st *= N;
+      }
+      c[e] = c2[(size_t)idx];
+    }
+    for (int s = 0; s < ns; ++s) {
+      int ss = s;
+      int64_t off = 0, st = 1;
+      bool ok = true;
+      int dl[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) {
+        dl[k] = ss % 3 - 1;
+        ss /= 3;
+        const int jk = i[k] + dl[k];
+        ok = ok && jk >= 0 && jk < n;
+        off += (int64_t)dl[k] * st;
+        st *= n;
+      }
+      if (!ok || off < 0) continue;
+      double S = 0.0;
+      for (int e = 0; e < (1 << d); ++e) {
+        bool in = true;
+        for (int k = 0; k < d; ++k) {
+          const int ek = (e >> k) & 1;
+          in = in && (dl[k] == 0 || (dl[k] == 1 && ek == 1) || (dl[k] == -1 && ek == 0));
+        }
+        if (in) S += c[e];
+      }
+      Kb[(size_t)(a * W + off)] = S * sc.ke[s];
+      Mb[(size_t)(a * W + off)] = sc.mtot[s];
+    }
+  }
+}
+
+std::vector<double> average_c2(int d, int Nf, const std::vector<double>& cf) {
+  const int Nc = Nf / 2;
+  int64_t ncc = 1;
+  for (int k = 0; k < d; ++k) ncc *= Nc;
+  std::vector<double> cc((size_t)ncc, 0.0);
+  for (int64_t a = 0; a < ncc; ++a) {
+    int ic[3] = {0, 0, 0};
+    int64_t r = a;
+    for (int k = 0; k < d; ++k) {
+      ic[k] = (int)(r % Nc);
+      r /= Nc;
+    }
+    double s = 0.0;
+    for (int e = 0; e < (1 << d); ++e) {
+      int64_t idx = 0, st = 1;
+      for (int k = 0; k < d; ++k) {
+        idx += (int64_t)(2 * ic[k] + ((e >> k) & 1)) * st;
+        st *= Nf;
+      }
+      s += cf[(size_t)idx];
+    }
+    cc[(size_t)a] = s / (1 << d);
+  }
+  return cc;
+}
+
+// ------------------------------------------------------------------ setup parts
+st_status setup_space_level(st_handle* h, int jx, SpaceLevel& sl) {
+  const st_problem& p = h->prob;
+  sl.jx = jx;
+  sl.geo = make_geo(p.d, jx);
+  for (int k = 0; k < p.d; ++k) sl.h[k] = (p.hi[k] - p.lo[k]) / (1 << jx);
+  sl.sc = make_coef(p.d, sl.h);
+  st_status s = eval_space(h, p.c2, cell_centres(p, jx), p.d, sl.c2h);
+  if (s != ST_OK) return s;
+  sl.c2min = 1e300;
+  for (double v : sl.c2h) {
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(h, ST_ERR_ARG, "c^2 must be positive and finite at every cell centre");
+    sl.c2min = std::min(sl.c2min, v);
+  }
+  sl.c2d = h->upload(sl.c2h);
+  ST_NEED(h, sl.c2d);
+  std::vector<float> cf(sl.c2h.begin(), sl.c2h.end());
+  sl.c2f = h->upload(cf);
+  ST_NEED(h, sl.c2f);
+  const std::vector<double> pts = node_points(p, jx);
+  sl.nall = (int64_t)pts.size() / p.d;
+  const int nrows = h->nterm_rows;
+  sl.loads = h->alloc<double>((size_t)nrows * sl.geo.nnodes);
+  ST_NEED(h, sl.loads);
+  double* tmp = h->alloc<double>((size_t)sl.nall);
+  ST_NEED(h, tmp);
+  std::vector<double> vals;
+  auto load_row = [&](const st_field& f, int row, double aK, double aM, bool keep_lift) -> st_status {
+    st_status s2 = eval_space(h, f, pts, p.d, vals);
+    if (s2 != ST_OK) return s2;
+    ST_CUDA(h, cudaMemcpyAsync(tmp, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->h2d_bytes += (int64_t)(vals.size() * sizeof(double));
+    launch_load(sl.geo, sl.sc, sl.c2d, tmp, sl.loads + (size_t)row * sl.geo.nnodes, aK, aM, 0, h->stream);
+    if (keep_lift && f.fn != nullptr) {
+      sl.lift = h->alloc<double>((size_t)sl.nall);
+      ST_NEED(h, sl.lift);
+      ST_CUDA(h, cudaMemcpyAsync(sl.lift, tmp, vals.size() * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    ST_CUDA(h, cudaStreamSynchronize(h->stream));
+    return check_launch(h, "load");
+  };
+  for (int r = 0; r < p.n_terms; ++r) {
+    st_field g{p.terms[r].g, p.terms[r].g_user};
+    if ((s = load_row(g, r, 0.0, 1.0, false)) != ST_OK) return s;
+  }
+  if ((s = load_row(p.v0, p.n_terms, 0.0, 1.0, false)) != ST_OK) return s;
+  if ((s = load_row(p.u0, p.n_terms + 1, 1.0, 0.0, true)) != ST_OK) return s;
+  return ST_OK;
+}
+
+st_status setup_time_level(st_handle* h, int jt, TimeData& td) {
+  const st_problem& p = h->prob;
+  build_time_level(jt, p.T, td.tl);
+  const int nt = td.tl.nt;
+  std::vector<double> Ab((size_t)nt * 5, 0.0), Bb((size_t)nt * 5, 0.0);
+  for (int i = 0; i < nt; ++i)
+    for (int t = -2; t <= 2; ++t) {
+      const int j = i + t;
+      if (j < 0 || j >= nt) continue;
+      Ab[(size_t)i * 5 + t + 2] = td.tl.A[(size_t)i * nt + j];
+      Bb[(size_t)i * 5 + t + 2] = td.tl.B[(size_t)i * nt + j];
+    }
+  td.Aband = h->upload(Ab);
+  td.Bband = h->upload(Bb);
+  ST_NEED(h, td.Aband);
+  ST_NEED(h, td.Bband);
+  // RHS time coefficient rows: (s_r, psi_i')_e, psi_i'(0), -(1, psi_i')_e.
+  const int nrows = h->nterm_rows;
+  std::vector<double> coef((size_t)nrows * nt, 0.0);
+  const int nq = (int)td.tl.qt.size();
+  std::vector<double> sv(nq);
+  for (int r = 0; r < p.n_terms; ++r) {
+    if (p.terms[r].s == nullptr) return fail(h, ST_ERR_ARG, "source term without time factor");
+    if (p.terms[r].s(nq, td.tl.qt.data(), sv.data(), p.terms[r].s_user) != 0)
+      return fail(h, ST_ERR_CALLBACK, "time callback failed");
+    for (int i = 0; i < nt; ++i) {
+      double acc = 0.0;
+      for (int q = 0; q < nq; ++q) acc += td.tl.Q[(size_t)i * nq + q] * sv[q];
+      coef[(size_t)r * nt + i] = acc;
+    }
+  }
+  for (int i = 0; i < nt; ++i) {
+    coef[(size_t)p.n_terms * nt + i] = td.tl.d0[i];
+    coef[(size_t)(p.n_terms + 1) * nt + i] = -td.tl.g1[i];
+  }
+  td.rhs_coef = h->upload(coef);
+  ST_NEED(h, td.rhs_coef);
+  return ST_OK;
+}
+
+// Coarsest multigrid level of a time-eigenbasis component: the coarsest grid
+// must resolve the largest wave number k = sqrt(-Re lam / min c^2) of its
+// modes (k h_c <= theta); grids with at most kMaxDirectRows unknowns are
+// solved directly.
+int choose_coarse(const st_problem& p, const Component& c) {
+  const int64_t nx = make_geo(p.d, c.jx).nnodes;
+  if (nx <= 1024) return c.jx;
+  double kmax = 0.0;
+  for (int q = 0; q < c.td->eig.nsel; ++q)
+    kmax = std::max(kmax, std::sqrt(std::max(0.0, -c.td->eig.lam[q].real()) / c.sl->c2min));
+  double L = 0.0;
+  for (int k = 0; k < p.d; ++k) L = std::max(L, p.hi[k] - p.lo[k]);
+  int jc = 2;
+  while (jc < c.jx && kmax * L / (1 << jc) > kThetaMG) ++jc;
+  int jmax = 1;  // largest level whose banded solve fits in shared memory
+  while (jmax + 1 <= c.jx && make_geo(p.d, jmax + 1).nnodes <= kMaxDirectRows) ++jmax;
+  if (jc >= c.jx) return nx <= kMaxDirectRows ? c.jx : jmax;
+  return std::min(jc, jmax);
+}
+
+// ||S||_2 <= ||A||_2 ||M||_2 + ||B||_2 ||K||_2 with ||X||_2 <= sqrt(||X||_1 ||X||_inf),
+// ||M||_2 <= max row sum = prod h_k and ||K||_2 <= max_a sum_b |K_ab|.
+double system_norm_bound(const Component& c) {
+  const TimeLevel& tl = c.td->tl;
+  const int nt = tl.nt;
+  auto n2 = [&](const std::vector<double>& X) {
+    double n1 = 0.0, ni = 0.0;
+    for (int i = 0; i < nt; ++i) {
+      double r = 0.0, cs = 0.0;
+      for (int j = 0; j < nt; ++j) {
+        r += std::fabs(X[(size_t)i * nt + j]);
+        cs += std::fabs(X[(size_t)j * nt + i]);
+      }
+      ni = std::max(ni, r);
+      n1 = std::max(n1, cs);
+    }
+    return std::sqrt(n1 * ni);
+  };
+  const Geo& g = c.sl->geo;
+  double mnorm = 1.0;
+  for (int k = 0; k < g.d; ++k) mnorm *= c.sl->h[k];
+  double c2max = 0.0;
+  for (double v : c.sl->c2h) c2max = std::max(c2max, v);
+  double knorm = 0.0;
+  const int ns = ipow3(g.d);
+  for (int s = 0; s < ns; ++s) {
+    int ss = s, zeros = 0;
+    for (int k = 0; k < g.d; ++k) {
+      if (ss % 3 == 1) ++zeros;
+      ss /= 3;
+    }
+    knorm += (double)(1 << zeros) * c2max * std::fabs(c.sl->sc.ke[s]);
+  }
+  return n2(tl.A) * mnorm + n2(tl.B) * knorm;
+}
+
+st_status setup_component(st_handle* h, Component& c) {
+  const st_problem& p = h->prob;
+  c.nx = c.sl->geo.nnodes;
+  c.nt = c.td->tl.nt;
+  c.Snorm = system_norm_bound(c);
+  const size_t n = (size_t)c.nx * c.nt;
+  c.F = h->alloc<double>(n);
+  c.U = h->alloc<double>(n);
+  c.Rv = h->alloc<double>(n);
+  c.KU = h->alloc<double>(n);
+  c.MU = h->alloc<double>(n);
+  ST_NEED(h, c.F);
+  ST_NEED(h, c.U);
+  ST_NEED(h, c.Rv);
+  ST_NEED(h, c.KU);
+  ST_NEED(h, c.MU);
+  if (p.f_general != nullptr) {
+    // time-projected general source on all nodes: sum_q Q[i][q] f(x, t_q)
+    const std::vector<double> pts = node_points(p, c.jx);
+    const int64_t nall = (int64_t)pts.size() / p.d;
+    const int nq = (int)c.td->tl.qt.size();
+    std::vector<double> acc((size_t)c.nt * nall, 0.0), fv(nall);
+    for (int q = 0; q < nq; ++q) {
+      if (p.f_general(nall, pts.data(), c.td->tl.qt[q], fv.data(), p.f_user) != 0)
+        return fail(h, ST_ERR_CALLBACK, "source callback failed");
+      for (int i = 0; i < c.nt; ++i) {
+        const double w = c.td->tl.Q[(size_t)i * nq + q];
+        if (w == 0.0) continue;
+        for (int64_t a = 0; a < nall; ++a) acc[(size_t)i * nall + a] += w * fv[a];
+      }
+    }
+    c.Fg_all = h->upload(acc);
+    ST_NEED(h, c.Fg_all);
+  }
+  if (c.method == 1) {
+    // space eigenbasis: dense K, M of the level, Phi, banded LU of A + mu B per spatial mode
+    const Geo& g = c.sl->geo;
+    const int bw = (int)band_width(g);
+    std::vector<double> Kb, Mb;
+    assemble_band(g, c.sl->sc, c.sl->c2h, Kb, Mb, bw);
+    const int nx = (int)c.nx;
+    std::vector<double> K((size_t)nx * nx, 0.0), M((size_t)nx * nx, 0.0);
+    for (int a = 0; a < nx; ++a)
+      for (int j = 0; j <= bw && a + j < nx; ++j) {
+        K[(size_t)(a + j) * nx + a] = K[(size_t)a * nx + a + j] = Kb[(size_t)a * (bw + 1) + j];
+        M[(size_t)(a + j) * nx + a] = M[(size_t)a * nx + a + j] = Mb[(size_t)a * (bw + 1) + j];
+      }
+    std::vector<double> mu, Phi;
+    if (!sym_gen_eig(nx, K, M, mu, Phi)) return fail(h, ST_ERR_NUMERIC, "spatial eigen-decomposition failed");
+    std::vector<double> PhiT((size_t)nx * nx);
+    for (int i = 0; i < nx; ++i)
+      for (int j = 0; j < nx; ++j) PhiT[(size_t)j * nx + i] = Phi[(size_t)i * nx + j];
+    c.Phi = h->upload(Phi);
+    c.PhiT = h->upload(PhiT);
+    ST_NEED(h, c.Phi);
+    ST_NEED(h, c.PhiT);
+    const int nt = c.nt, kl = 2, ku = 2, ld = 2 * kl + ku + 1;
+    std::vector<double> abAll((size_t)ld * nt * nx, 0.0);
+    std::vector<int> pivAll((size_t)nt * nx, 0);
+    std::vector<double> ab((size_t)ld * nt);
+    std::vector<int> piv;
+    for (int a = 0; a < nx; ++a) {
+      std::fill(ab.begin(), ab.end(), 0.0);
+      for (int j = 0; j < nt; ++j)
+        for (int i = std::max(0, j - ku); i <= std::min(nt - 1, j + kl); ++i)
+          ab[(size_t)(kl + ku + i - j) + (size_t)j * ld] =
+              c.td->tl.A[(size_t)i * nt + j] + mu[a] * c.td->tl.B[(size_t)i * nt + j];
+      if (!band_lu(nt, kl, ku, ab, piv)) return fail(h, ST_ERR_NUMERIC, "time band LU failed");
+      for (size_t e = 0; e < ab.size(); ++e) abAll[e * nx + a] = ab[e];
+      for (int j = 0; j < nt; ++j) pivAll[(size_t)j * nx + a] = piv[j];
+    }
+    c.ab = h->upload(abAll);
+    c.piv = h->upload(pivAll);
+    ST_NEED(h, c.ab);
+    ST_NEED(h, c.piv);
+    c.kl = kl;
+    c.ku = ku;
+    ST_CUDA(h, cudaStreamSynchronize(h->stream));
+    return ST_OK;
+  }
+  // time eigenbasis
+  c.nsel = c.td->eig.nsel;
+  c.inner64 = (h->opt.precision == ST_FP64) || (c.td->eig.cond_est > kKappaFP32);
+  c.jc = choose_coarse(p, c);
+  c.direct = (c.jc == c.jx);
+  // multigrid hierarchy jx -> jc (level 0 uses the sampled c^2)
+  c.mg.clear();
+  {
+    MGLevel l0;
+    l0.j = c.jx;
+    l0.geo = c.sl->geo;
+    l0.sc = c.sl->sc;
+    l0.c2h = c.sl->c2h;
+    l0.c2d = c.sl->c2d;
+    l0.c2f = c.sl->c2f;
+    c.mg.push_back(l0);
+  }
+  for (int j = c.jx - 1; j >= c.jc; --j) {
+    MGLevel l;
+    l.j = j;
+    l.geo = make_geo(p.d, j);
+    double hh[3];
+    for (int k = 0; k < p.d; ++k) hh[k] = (p.hi[k] - p.lo[k]) / (1 << j);
+    l.sc = make_coef(p.d, hh);
+    l.c2h = average_c2(p.d, 1 << (j + 1), c.mg.back().c2h);
+    l.c2d = h->upload(l.c2h);
+    std::vector<float> cf(l.c2h.begin(), l.c2h.end());
+    l.c2f = h->upload(cf);
+    ST_NEED(h, l.c2d);
+    ST_NEED(h, l.c2f);
+    c.mg.push_back(std::move(l));
+  }
+  const MGLevel& lc = c.mg.back();
+  c.bw = (int)band_width(lc.geo);
+  c.nrowc = lc.geo.nnodes;
+  assemble_band(lc.geo, lc.sc, lc.c2h, c.Kband, c.Mband, c.bw);
+  c.Kb = h->upload(c.Kband);
+  c.Mb = h->upload(c.Mband);
+  ST_NEED(h, c.Kb);
+  ST_NEED(h, c.Mb);
+  c.scal = h->alloc<CocgScal>(c.nsel);
+  c.part = h->alloc<double>((size_t)c.nsel * 304 * 2);
+  ST_NEED(h, c.scal);
+  ST_NEED(h, c.part);
+  c.scal_h.resize(c.nsel);
+  return ST_OK;
+}
+
+template <typename R> Work<R>& work_of(Component& c);
+template <> Work<double>& work_of<double>(Component& c) { return c.w64; }
+template <> Work<float>& work_of<float>(Component& c) { return c.w32; }
+template <typename R> const R* c2_of(const MGLevel& l);
+template <> const double* c2_of<double>(const MGLevel& l) { return l.c2d; }
+template <> const float* c2_of<float>(const MGLevel& l) { return l.c2f; }
+
+template <typename R> st_status prepare_work(st_handle* h, Component& c) {
+  Work<R>& w = work_of<R>(c);
+  if (w.ready) return ST_OK;
+  const size_t n0 = (size_t)c.nsel * c.nx;
+  w.G = h->alloc<cx<R>>(n0);
+  w.X = h->alloc<cx<R>>(n0);
+  ST_NEED(h, w.G);
+  ST_NEED(h, w.X);
+  if (!c.direct) {
+    w.Rr = h->alloc<cx<R>>(n0);
+    w.P = h->alloc<cx<R>>(n0);
+    w.Wv = h->alloc<cx<R>>(n0);
+    w.Z = h->alloc<cx<R>>(n0);
+    w.T0 = h->alloc<cx<R>>(n0);
+    w.R0 = h->alloc<cx<R>>(n0);
+    ST_NEED(h, w.Rr);
+    ST_NEED(h, w.P);
+    ST_NEED(h, w.Wv);
+    ST_NEED(h, w.Z);
+    ST_NEED(h, w.T0);
+    ST_NEED(h, w.R0);
+    const int L = (int)c.mg.size();
+    w.bl.assign(L, nullptr);
+    w.rl.assign(L, nullptr);
+    w.xa.assign(L, nullptr);
+    w.xb.assign(L, nullptr);
+    for (int l = 1; l < L; ++l) {
+      const size_t nl = (size_t)c.nsel * c.mg[l].geo.nnodes;
+      w.bl[l] = h->alloc<cx<R>>(nl);
+      w.rl[l] = h->alloc<cx<R>>(nl);
+      w.xa[l] = h->alloc<cx<R>>(nl);
+      w.xb[l] = h->alloc<cx<R>>(nl);
+      ST_NEED(h, w.bl[l]);
+      ST_NEED(h, w.rl[l]);
+      ST_NEED(h, w.xa[l]);
+      ST_NEED(h, w.xb[l]);
+    }
+  }
+  // coarsest-level factorisations, one per mode
+  w.band = h->alloc<cx<R>>((size_t)c.nsel * c.nrowc * (c.bw + 1));
+  ST_NEED(h, w.band);
+  const cx<double>* lam64 = c.td->lam64;
+  launch_band_form<R>(c.Kb, c.Mb, lam64, w.band, c.nrowc, c.bw, c.nsel, h->stream);
+  ST_CUDA(h, cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+  launch_band_ldlt<R>(w.band, c.nrowc, c.bw, c.nsel, h->dev_err, h->stream);
+  int herr = 0;
+  ST_CUDA(h, cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  st_status s = check_launch(h, "band factorisation");
+  if (s != ST_OK) return s;
+  if (herr) return fail(h, ST_ERR_NUMERIC, "zero pivot in a banded LDL^T factorisation");
+  w.ready = true;
+  return ST_OK;
+}
+
+template <typename R> const cx<R>* lam_of(const TimeData& td);
+template <> const cx<double>* lam_of<double>(const TimeData& td) { return td.lam64; }
+template <> const cx<float>* lam_of<float>(const TimeData& td) { return td.lam32; }
+
+double omega_of(int d) { return d == 1 ? kOmega1D : (d == 2 ? kOmega2D : kOmega3D); }
+
+// x = B_mg b on level l; two Jacobi sweeps before and after the coarse correction.
+// Returns the buffer holding the result (always xb).
+template <typename R>
+cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R>* xb, cx<R>* rtmp) {
+  Work<R>& w = work_of<R>(c);
+  const MGLevel& lv = c.mg[l];
+  const cx<R>* lam = lam_of<R>(*c.td);
+  const int64_t n = lv.geo.nnodes;
+  cudaStream_t s = h->stream;
+  const int L = (int)c.mg.size() - 1;
+  const double m = (double)c.nactive, cs = sizeof(cx<R>), rs = sizeof(R);
+  const double fl = stencil_flops(lv.geo.d);
+  if (l == L) {
+    PROF(h, KC_BAND_SOLVE, m * (double)n * ((c.bw + 1) * cs + 2 * cs), m * (double)n * c.bw * 16.0,
+         launch_band_solve<R>(w.band, c.nrowc, c.bw, b, xb, c.scal, c.nsel, n, s));
+    return xb;
+  }
+  const double om = omega_of(lv.geo.d);
+  const R* c2 = c2_of<R>(lv);
+  const double cb = (double)lv.geo.ncells * rs;
+  PROF(h, KC_JACOBI, m * n * 2 * cs + cb, m * n * 30.0,
+       launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, lv.sc, c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
+  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
+  PROF(h, KC_MG_RESID, m * n * 3 * cs + cb, m * n * (fl + 2.0),
+       launch_stencil<R>(OP_RESID, lv.geo, lv.sc, c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
+  const MGLevel& lc = c.mg[l + 1];
+  const double nc = (double)lc.geo.nnodes;
+  PROF(h, KC_RESTRICT, m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
+       launch_restrict<R>(lv.geo, lc.geo, rtmp, w.bl[l + 1], c.scal, c.nsel, n, lc.geo.nnodes, s));
+  cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
+  PROF(h, KC_PROLONG, m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
+       launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
+  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
+  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
+  return xb;
+}
+
+// Solve (lam_q M + K) x_q = g_q for every mode; w.G holds g, the result lands in w.X.
+template <typename R> st_status inner_solve(st_handle* h, Component& c, int& iters_out) {
+  Work<R>& w = work_of<R>(c);
+  cudaStream_t s = h->stream;
+  const int64_t n = c.nx;
+  const double cs = sizeof(cx<R>), rs = sizeof(R);
+  iters_out = 0;
+  c.nactive = c.nsel;
+  if (c.direct) {
+    const double m = c.nsel;
+    PROF(h, KC_BAND_SOLVE, m * (double)n * ((c.bw + 1) * cs + 2 * cs), m * (double)n * c.bw * 16.0,
+         launch_band_solve<R>(w.band, c.nrowc, c.bw, w.G, w.X, nullptr, c.nsel, n, s));
+    return check_launch(h, "direct band solve");
+  }
+  const double tol = sizeof(R) == 8 ? 1e-12 : 1e-5;
+  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  const MGLevel& l0 = c.mg[0];
+  const R* c2 = c2_of<R>(l0);
+  const cx<R>* lam = lam_of<R>(*c.td);
+  const double fl = stencil_flops(l0.geo.d), cb = (double)l0.geo.ncells * rs;
+  PROF(h, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
+       launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
+  // z = B r ; rho = r . z ; p = z
+  cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
+  PROF(h, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
+       launch_dot<R>(2, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+  PROF(h, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0,
+       launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
+  const int check_every = 4;
+  for (int it = 1; it <= max_iter; ++it) {
+    const double m = c.nactive;
+    PROF(h, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
+         launch_stencil<R>(OP_APPLY, l0.geo, l0.sc, c2, w.P, nullptr, w.Wv, lam, c.scal, c.nsel, n, 0.0, s));
+    PROF(h, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+         launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+    PROF(h, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
+         launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+    if (it % check_every == 0 || it == max_iter) {
+      ST_CUDA(h, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
+      h->d2h_bytes += (int64_t)(c.nsel * sizeof(CocgScal));
+      ST_CUDA(h, cudaStreamSynchronize(s));
+      st_status st = check_launch(h, "cocg");
+      if (st != ST_OK) return st;
+      int na = 0;
+      for (const auto& q : c.scal_h) na += q.active ? 1 : 0;
+      c.nactive = na;
+      if (na == 0) break;
+    }
+    z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
+    PROF(h, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+         launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+    PROF(h, KC_UPDATE, m * n * 3 * cs, m * n * 8.0,
+         launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+  }
+  ST_CUDA(h, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
+  ST_CUDA(h, cudaStreamSynchronize(s));
+  int worst = 0;
+  for (const auto& q : c.scal_h) {
+    iters_out = std::max(iters_out, q.iters);
+    if (q.status != 0) worst = q.status;
+  }
+  if (worst == 4) return fail(h, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
+  if (worst != 0) return fail(h, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
+  return ST_OK;
+}
+
+st_status assemble_rhs(st_handle* h, Component& c) {
+  if (c.f_ready) return ST_OK;
+  PROF(h, KC_RHS, (double)(h->nterm_rows + c.nt) * c.nx * 8.0, 2.0 * h->nterm_rows * c.nt * (double)c.nx,
+       launch_rhs_assemble(c.td->rhs_coef, c.sl->loads, c.F, h->nterm_rows, c.nt, c.nx, h->stream));
+  if (c.Fg_all != nullptr)
+    for (int i = 0; i < c.nt; ++i)
+      launch_load(c.sl->geo, c.sl->sc, c.sl->c2d, c.Fg_all + (size_t)i * c.sl->nall, c.F + (size_t)i * c.nx, 0.0,
+                  1.0, 1, h->stream);
+  c.f_ready = true;
+  return check_launch(h, "rhs");
+}
+
+st_status read_norm(st_handle* h, const double* v, int64_t n, double& out) {
+  PROF(h, KC_NORM, (double)n * 8.0, 2.0 * n, launch_norm2(v, n, h->part, h->scalar, h->stream));
+  ST_CUDA(h, cudaMemcpyAsync(h->scalar_h, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  h->d2h_bytes += (int64_t)sizeof(double);
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  out = std::sqrt(*h->scalar_h);
+  return check_launch(h, "norm");
+}
+
+template <typename R> st_status sweep_time_eig(st_handle* h, Component& c, const double* Rin, int& iters) {
+  st_status s = prepare_work<R>(h, c);
+  if (s != ST_OK) return s;
+  Work<R>& w = work_of<R>(c);
+  const double cs = sizeof(cx<R>), nx = (double)c.nx;
+  PROF(h, KC_TRANSFORM, c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+       launch_fwd_transform<R>(c.td->W, Rin, w.G, c.nsel, c.nt, c.nx, h->stream));
+  s = inner_solve<R>(h, c, iters);
+  if (s != ST_OK) return s;
+  PROF(h, KC_TRANSFORM, 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+       launch_back_transform<R>(c.td->V, c.td->wq, w.X, c.U, c.nsel, c.nt, c.nx, h->stream));
+  return check_launch(h, "time transforms");
+}
+
+st_status sweep_space_eig(st_handle* h, Component& c, const double* Rin) {
+  const double nx = (double)c.nx, nt = c.nt;
+  PROF(h, KC_SPACE_EIG, (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+       launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, h->stream));
+  PROF(h, KC_SPACE_EIG, (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
+       launch_time_band_solve(c.ab, c.piv, c.KU, c.nt, c.nx, c.kl, c.ku, h->stream));
+  PROF(h, KC_SPACE_EIG, (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+       launch_gemm_right(c.KU, c.PhiT, c.U, c.nt, c.nx, 1, 1, h->stream));
+  return check_launch(h, "space eigenbasis sweep");
+}
+
+st_status solve_one(st_handle* h, Component& c) {
+  st_status s = assemble_rhs(h, c);
+  if (s != ST_OK) return s;
+  const size_t n = (size_t)c.nx * c.nt;
+  ST_CUDA(h, cudaMemsetAsync(c.U, 0, n * sizeof(double), h->stream));
+  double fn = 0.0;
+  if ((s = read_norm(h, c.F, (int64_t)n, fn)) != ST_OK) return s;
+  // Refinement stops on the normwise backward error eta = ||R|| / (||S|| ||U|| + ||F||)
+  // (the relative residual of an exact solution can be far above rounding
+  // when S is ill-conditioned), or when a sweep no longer halves eta.
+  const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-14;
+  const int max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 8;
+  c.info = st_solve_info{};
+  c.info.status = ST_OK;
+  if (fn == 0.0) {
+    c.solved = true;
+    return ST_OK;
+  }
+  double rel = 1.0, eta = 1.0, eta_prev = 1e300;
+  const double* Rin = c.F;
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    int iters = 0;
+    if (c.method == 1) {
+      s = sweep_space_eig(h, c, Rin);
+    } else if (c.inner64) {
+      s = sweep_time_eig<double>(h, c, Rin, iters);
+    } else {
+      s = sweep_time_eig<float>(h, c, Rin, iters);
+    }
+    if (s != ST_OK) {
+      c.info.status = s;
+      return s;
+    }
+    c.info.sweeps = sw + 1;
+    c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
+    PROF(h, KC_RESIDUAL64, 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
+         (double)n * (4.0 * ipow3(c.sl->geo.d) + 20.0),
+         launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, c.U, c.F, c.td->Aband, c.td->Bband, c.KU, c.MU, c.Rv, c.nt,
+                         h->stream));
+    double rn = 0.0, un = 0.0;
+    if ((s = read_norm(h, c.Rv, (int64_t)n, rn)) != ST_OK) return s;
+    if ((s = read_norm(h, c.U, (int64_t)n, un)) != ST_OK) return s;
+    rel = rn / fn;
+    eta = rn / (c.Snorm * un + fn);
+    if (!std::isfinite(rel)) {
+      c.info.status = ST_ERR_NUMERIC;
+      return fail(h, ST_ERR_NUMERIC, "non-finite residual");
+    }
+    if (eta <= tol || eta > 0.5 * eta_prev) break;
+    eta_prev = eta;
+    Rin = c.Rv;
+  }
+  c.info.rel_residual = rel;
+  c.info.backward_error = eta;
+  c.solved = true;
+  if (eta > 1e3 * tol && eta > 1e-12) {
+    c.info.status = ST_ERR_NOT_CONVERGED;
+    return fail(h, ST_ERR_NOT_CONVERGED, "refinement did not reach the backward-error target");
+  }
+  return ST_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+st_status st_setup(const st_problem* problem, const st_options* options, st_handle** out) {
+  if (out == nullptr || problem == nullptr) return fail(nullptr, ST_ERR_ARG, "null argument");
+  *out = nullptr;
+  const st_problem& p = *problem;
+  if (p.d < 1 || p.d > 3) return fail(nullptr, ST_ERR_ARG, "d must be 1, 2 or 3");
+  if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(nullptr, ST_ERR_ARG, "T must be positive");
+  for (int k = 0; k < p.d; ++k)
+    if (!(p.hi[k] > p.lo[k])) return fail(nullptr, ST_ERR_ARG, "empty box");
+  if (p.J < 0 || p.mx < 1 || p.mt < 0) return fail(nullptr, ST_ERR_ARG, "levels: need J >= 0, mx >= 1, mt >= 0");
+  if (p.c2.fn == nullptr) return fail(nullptr, ST_ERR_ARG, "c^2 callback is required");
+  if (p.n_terms < 0 || (p.n_terms > 0 && p.terms == nullptr)) return fail(nullptr, ST_ERR_ARG, "bad source terms");
+  const int jx_max = p.mx + p.J, jt_max = p.mt + p.J;
+  const int cap = p.d == 1 ? 20 : (p.d == 2 ? 13 : 9);
+  if (jx_max > cap || jt_max > 14) return fail(nullptr, ST_ERR_ARG, "level too large for this build");
+  auto h = std::make_unique<st_handle>();
+  h->prob = p;
+  if (options) h->opt = *options;
+  if (h->opt.precision != ST_FP64 && h->opt.precision != ST_FP32_IR)
+    return fail(nullptr, ST_ERR_ARG, "unknown precision");
+  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  h->nterm_rows = p.n_terms + 2;
+  h->launches0 = kernel_launch_count();
+  st_handle* hp = h.get();
+  hp->part = hp->alloc<double>(304);
+  hp->scalar = hp->alloc<double>(1);
+  hp->dev_err = hp->alloc<int>(1);
+  if (!hp->part || !hp->scalar || !hp->dev_err) {
+    g_create_error = "device allocation failed";
+    return ST_ERR_OOM;
+  }
+  if (cudaMallocHost(&hp->scalar_h, sizeof(double)) != cudaSuccess) {
+    g_create_error = "pinned allocation failed";
+    return ST_ERR_CUDA;
+  }
+  // Components of Eq. (19)
+  std::vector<std::tuple<int, int, int>> cl;
+  {
+    std::vector<int> lst(3 * (2 * p.J + 1));
+    st_host_components(p.J, p.mx, p.mt, lst.data());
+    for (int k = 0; k < 2 * p.J + 1; ++k) cl.emplace_back(lst[3 * k], lst[3 * k + 1], lst[3 * k + 2]);
+  }
+  for (auto& t : cl) {
+    const int jx = std::get<0>(t), jt = std::get<1>(t);
+    if (!hp->space.count(jx)) {
+      auto sl = std::make_unique<SpaceLevel>();
+      st_status s = setup_space_level(hp, jx, *sl);
+      if (s != ST_OK) {
+        g_create_error = hp->err;
+        return s;
+      }
+      hp->space[jx] = std::move(sl);
+    }
+    const int nt = (1 << jt) + 1;
+    const int64_t nx = make_geo(p.d, jx).nnodes;
+    const bool space_eig = nt > kModeTMaxNt && nx <= kModeSMaxNx;
+    if (!hp->time.count(jt)) {
+      auto td = std::make_unique<TimeData>();
+      st_status s = setup_time_level(hp, jt, *td);
+      if (s != ST_OK) {
+        g_create_error = hp->err;
+        return s;
+      }
+      hp->time[jt] = std::move(td);
+    }
+    TimeData& td = *hp->time[jt];
+    if (!space_eig && !td.have_eig) {
+      if (!time_eig(td.tl, td.eig)) {
+        g_create_error = "eigen-decomposition of the time matrices failed";
+        return ST_ERR_NUMERIC;
+      }
+      td.have_eig = true;
+      // upload
+      const int ns = td.eig.nsel, ntt = td.tl.nt;
+      std::vector<cx<double>> Wc((size_t)ns * ntt), Vc((size_t)ntt * ns), lc(ns);
+      std::vector<cx<float>> lf(ns);
+      for (size_t e = 0; e < Wc.size(); ++e) Wc[e] = mk(td.eig.W[e].real(), td.eig.W[e].imag());
+      for (size_t e = 0; e < Vc.size(); ++e) Vc[e] = mk(td.eig.V[e].real(), td.eig.V[e].imag());
+      for (int q = 0; q < ns; ++q) {
+        lc[q] = mk(td.eig.lam[q].real(), td.eig.lam[q].imag());
+        lf[q] = mk((float)td.eig.lam[q].real(), (float)td.eig.lam[q].imag());
+      }
+      td.W = hp->upload(Wc);
+      td.V = hp->upload(Vc);
+      td.lam64 = hp->upload(lc);
+      td.lam32 = hp->upload(lf);
+      td.wq = hp->upload(td.eig.weight);
+      if (!td.W || !td.V || !td.lam64 || !td.lam32 || !td.wq) {
+        g_create_error = "device allocation failed";
+        return ST_ERR_OOM;
+      }
+    }
+    auto c = std::make_unique<Component>();
+    c->jx = jx;
+    c->jt = jt;
+    c->coef = std::get<2>(t);
+    c->method = space_eig ? 1 : 0;
+    c->sl = hp->space[jx].get();
+    c->td = &td;
+    st_status s = setup_component(hp, *c);
+    if (s != ST_OK) {
+      g_create_error = hp->err;
+      return s;
+    }
+    hp->comps.push_back(std::move(c));
+  }
+  if (cudaStreamSynchronize(hp->stream) != cudaSuccess) {
+    g_create_error = "stream synchronisation failed during setup";
+    return ST_ERR_CUDA;
+  }
+  *out = h.release();
+  return ST_OK;
+}
+
+st_status st_num_components(const st_handle* h, int* n) {
+  if (!h || !n) return ST_ERR_ARG;
+  *n = (int)h->comps.size();
+  return ST_OK;
+}
+
+st_status st_component(const st_handle* h, int k, st_component_info* info) {
+  if (!h || !info || k < 0 || k >= (int)h->comps.size()) return ST_ERR_ARG;
+  const Component& c = *h->comps[k];
+  info->jx = c.jx;
+  info->jt = c.jt;
+  info->coef = c.coef;
+  info->n_space = c.nx;
+  info->n_time = c.nt;
+  info->method = c.method;
+  info->n_modes = c.method == 1 ? (int)c.nx : c.nsel;
+  return ST_OK;
+}
+
+st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
+  if (!h) return ST_ERR_ARG;
+  if (k < -1 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
+  st_status worst = ST_OK;
+  st_solve_info agg{};
+  const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? (int)h->comps.size() : k + 1;
+  for (int i = k0; i < k1; ++i) {
+    st_status s = solve_one(h, *h->comps[i]);
+    const st_solve_info& ci = h->comps[i]->info;
+    agg.sweeps = std::max(agg.sweeps, ci.sweeps);
+    agg.max_inner_iters = std::max(agg.max_inner_iters, ci.max_inner_iters);
+    agg.rel_residual = std::max(agg.rel_residual, ci.rel_residual);
+    agg.backward_error = std::max(agg.backward_error, ci.backward_error);
+    if (s != ST_OK) {
+      worst = s;
+      break;
+    }
+  }
+  agg.status = worst;
+  if (info) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+    *info = agg;
+  }
+  return worst;
+}
+
+st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
+  if (!h || !out_dev) return ST_ERR_ARG;
+  if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
+  for (auto& c : h->comps)
+    if (!c->solved) return fail(h, ST_ERR_STATE, "combine before every component is solved");
+  const st_problem& p = h->prob;
+  const int nc = (int)h->comps.size(), nts = (1 << jt_star) + 1;
+  auto key = std::make_pair(jx_star, jt_star);
+  if (!h->comb.count(key)) {
+    // Components sorted by their combination level min(jx, jx*); B-spline tables
+    // of every component at every target time; partial-sum buffers per level.
+    std::vector<int> order(nc);
+    for (int c = 0; c < nc; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return std::min(h->comps[a]->jx, jx_star) < std::min(h->comps[b]->jx, jx_star);
+    });
+    std::vector<CombComp> cc(nc);
+    std::vector<double> tb((size_t)nc * nts * 3);
+    std::vector<int> tsp((size_t)nc * nts);
+    st_handle::CombTables t;
+    t.jmin = jx_star;
+    for (int o = 0; o < nc; ++o) {
+      const Component& k = *h->comps[order[o]];
+      cc[o] = CombComp{k.U, k.sl->lift, k.jx, k.jt, k.coef, 0};
+      const int lev = std::min(k.jx, jx_star);
+      t.jmin = std::min(t.jmin, lev);
+      const int Nt = 1 << k.jt;
+      for (int s = 0; s < nts; ++s) {
+        int span = (k.jt >= jt_star) ? (s << (k.jt - jt_star)) : (s >> (jt_star - k.jt));
+        span = std::min(span, Nt - 1);
+        const double tt = p.T * (double)s / (double)(1 << jt_star);
+        double v[3], d1[3], d2[3];
+        bspline_local(Nt, p.T, span, tt, v, d1, d2);
+        for (int a = 0; a < 3; ++a) tb[((size_t)o * nts + s) * 3 + a] = v[a];
+        tsp[(size_t)o * nts + s] = span;
+      }
+    }
+    t.first.assign(jx_star + 2, nc);
+    for (int o = nc - 1; o >= 0; --o) {
+      const int lev = std::min(cc[o].jx, jx_star);
+      t.first[lev] = o;
+    }
+    for (int lev = jx_star; lev >= 0; --lev) t.first[lev] = std::min(t.first[lev], t.first[lev + 1]);
+    t.comps = h->alloc<CombComp>(nc);
+    t.tb = h->alloc<double>(tb.size());
+    t.span = h->alloc<int>(tsp.size());
+    if (!t.comps || !t.tb || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
+    t.Y.assign(jx_star + 1, nullptr);
+    for (int lev = t.jmin; lev < jx_star; ++lev) {
+      int64_t nsp = 1;
+      for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
+      t.Y[lev] = h->alloc<double>((size_t)nsp * nts);
+      if (!t.Y[lev]) return fail(h, ST_ERR_OOM, "device allocation failed");
+    }
+    ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
+    ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    ST_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->comb[key] = t;
+  }
+  const st_handle::CombTables& t = h->comb[key];
+  for (int lev = t.jmin; lev <= jx_star; ++lev) {
+    const int c0 = t.first[lev], c1 = t.first[lev + 1];
+    const double* Yp = lev > t.jmin ? t.Y[lev - 1] : nullptr;
+    double* Y = lev == jx_star ? out_dev : t.Y[lev];
+    int64_t nsp = 1;
+    for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
+    const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
+    PROF(h, KC_COMBINE, outb + inb, (double)nsp * nts * (2.0 * (1 << p.d) + 8.0 * (c1 - c0)),
+         launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
+  }
+  return check_launch(h, "combine");
+}
+
+st_status st_component_coeffs(st_handle* h, int k, double* host_out) {
+  if (!h || !host_out || k < 0 || k >= (int)h->comps.size()) return ST_ERR_ARG;
+  Component& c = *h->comps[k];
+  if (!c.solved) return fail(h, ST_ERR_STATE, "component not solved");
+  ST_CUDA(h, cudaMemcpyAsync(host_out, c.U, (size_t)c.nx * c.nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+st_status st_total_dofs(const st_handle* h, int64_t* dofs) {
+  if (!h || !dofs) return ST_ERR_ARG;
+  int64_t s = 0;
+  for (auto& c : h->comps) s += c->nx * c->nt;
+  *dofs = s;
+  return ST_OK;
+}
+
+st_status st_transfer_bytes(const st_handle* h, int64_t* h2d, int64_t* d2h) {
+  if (!h) return ST_ERR_ARG;
+  if (h2d) *h2d = h->h2d_bytes;
+  if (d2h) *d2h = h->d2h_bytes;
+  return ST_OK;
+}
+
+st_status st_kernel_launches(const st_handle* h, int64_t* count) {
+  if (!h || !count) return ST_ERR_ARG;
+  *count = kernel_launch_count() - h->launches0;
+  return ST_OK;
+}
+
+st_status st_profile(st_handle* h, int enable) {
+  if (!h) return ST_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+  for (auto& r : h->prof) {
+    h->ev_pool.push_back(r.a);
+    h->ev_pool.push_back(r.b);
+  }
+  h->prof.clear();
+  h->prof_on = enable != 0;
+  return ST_OK;
+}
+
+st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n_out) {
+  if (!h || !n_out) return ST_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+  st_kernel_stat agg[KC_COUNT];
+  std::memset(agg, 0, sizeof(agg));
+  for (auto& r : h->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return fail(h, ST_ERR_CUDA, "event timing failed");
+    agg[r.cls].launches += 1;
+    agg[r.cls].ms += ms;
+    agg[r.cls].bytes += r.bytes;
+    agg[r.cls].flops += r.flops;
+  }
+  int n = 0;
+  for (int k = 0; k < KC_COUNT; ++k) {
+    if (agg[k].launches == 0) continue;
+    if (out && n < max_out) {
+      out[n] = agg[k];
+      std::snprintf(out[n].name, sizeof(out[n].name), "%s", kClassName[k]);
+    }
+    ++n;
+  }
+  *n_out = n;
+  return ST_OK;
+}
+
+st_status st_destroy(st_handle* h) {
+  if (!h) return ST_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  delete h;
+  return ST_OK;
+}
+
+const char* st_last_error(const st_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

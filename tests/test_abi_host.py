@@ -1,0 +1,110 @@
+"""CPU tests of the C ABI library: it builds, loads, exports every declared
+symbol, and its host-side setup math matches the oracle (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import st_workloads as W
+from oracle import combination, space, timemats
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_09688_gb300 import build
+    path = build.build(force=False)
+    L = C.CDLL(path)
+    L.st_host_time_matrices.argtypes = [C.c_int, C.c_double] + [C.c_void_p] * 4
+    L.st_host_time_eig.argtypes = [C.c_int, C.c_double, C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]
+    L.st_host_components.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p]
+    L.st_host_sym_gen_eig.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    return L
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = set()
+    for hdr in ("st.h", "st_host.h"):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(st_\w+)\s*\(", text))
+    assert len(names) >= 14
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("jt,T", [(0, 1.0), (1, 1.0), (3, 1.0), (5, 2.5), (7, 1.0)])
+def test_time_matrices_match_oracle(lib, jt, T):
+    nt = (1 << jt) + 1
+    A, B = np.zeros((nt, nt)), np.zeros((nt, nt))
+    g1, d0 = np.zeros(nt), np.zeros(nt)
+    assert lib.st_host_time_matrices(jt, T, _ptr(A), _ptr(B), _ptr(g1), _ptr(d0)) == 0
+    Ao, Bo = timemats.time_matrices(jt, T)
+    assert np.allclose(A, Ao, rtol=1e-13, atol=1e-13 * np.abs(Ao).max())
+    assert np.allclose(B, Bo, rtol=1e-13, atol=1e-13 * np.abs(Bo).max())
+    assert np.allclose(g1, timemats.load_one(jt, T), atol=1e-14)
+    assert np.allclose(d0, timemats.dpsi_at_zero(jt, T), atol=1e-12)
+
+
+@pytest.mark.parametrize("J,mx,mt", [(0, 1, 1), (3, 2, 1), (8, 2, 2)])
+def test_component_list_matches_oracle(lib, J, mx, mt):
+    out = np.zeros(3 * (2 * J + 1), dtype=np.int32)
+    assert lib.st_host_components(J, mx, mt, _ptr(out)) == 0
+    assert [tuple(r) for r in out.reshape(-1, 3)] == combination.components(J, mx, mt)
+
+
+@pytest.mark.parametrize("jt", [1, 2, 4, 6])
+def test_time_eigenvalues_match_numpy(lib, jt):
+    nt = (1 << jt) + 1
+    lam = np.zeros(2 * nt)
+    nsel, cond, res = C.c_int(), C.c_double(), C.c_double()
+    assert lib.st_host_time_eig(jt, 1.0, C.byref(nsel), _ptr(lam), C.byref(cond), C.byref(res)) == 0
+    got = lam[:2 * nsel.value].reshape(-1, 2)
+    got = got[:, 0] + 1j * got[:, 1]
+    A, B = timemats.time_matrices(jt, 1.0)
+    ref = np.linalg.eigvals(np.linalg.solve(B, A))
+    full = np.concatenate([got, np.conj(got[np.abs(got.imag) > 0])])
+    assert len(full) == nt
+    scale = np.abs(ref).max()
+    for z in ref:
+        assert np.min(np.abs(full - z)) < 1e-9 * scale
+    assert res.value < 1e-12
+    assert cond.value < 1e7
+
+
+def test_generalised_symmetric_eig_matches_scipy(lib):
+    p = W.layered_2d(6, 3)
+    sm = space.space_matrices(p, 3)
+    K, M = sm["K"].toarray(), sm["M"].toarray()
+    n = K.shape[0]
+    mu, Phi = np.zeros(n), np.zeros((n, n))
+    assert lib.st_host_sym_gen_eig(n, _ptr(np.ascontiguousarray(K)), _ptr(np.ascontiguousarray(M)),
+                                   _ptr(mu), _ptr(Phi)) == 0
+    assert np.allclose(np.sort(mu), sla.eigh(K, M, eigvals_only=True), rtol=1e-10)
+    assert np.allclose(Phi.T @ M @ Phi, np.eye(n), atol=1e-10)
+    assert np.allclose(Phi.T @ K @ Phi, np.diag(mu), atol=1e-8 * mu.max())
+
+
+def test_setup_rejects_bad_arguments_without_touching_the_gpu():
+    from paper_2606_09688_gb300 import st as B
+    L = B.lib()
+    prob = B.StProblem()
+    prob.d = 4
+    h = C.c_void_p()
+    assert L.st_setup(C.byref(prob), None, C.byref(h)) == B.ST_ERR_ARG
+    assert b"d must be" in L.st_last_error(None)
+    prob.d = 2
+    prob.hi[0] = prob.hi[1] = 1.0
+    prob.T = 1.0
+    prob.mx = 1
+    assert L.st_setup(C.byref(prob), None, C.byref(h)) == B.ST_ERR_ARG   # no c^2 callback
+    assert h.value is None

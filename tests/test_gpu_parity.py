@@ -1,0 +1,136 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: the plain FP64 path must match the oracle's combined solution to
+1e-10 relative l2 on the target grid; the FP32 + FP64-refinement path to 1e-8.
+Component coefficient arrays are compared too (same scale).
+"""
+import numpy as np
+import pytest
+
+import st_workloads as W
+from oracle import solve as osolve
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_09688_gb300 import build
+    build.build(force=False)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run(p, precision, target, method="lu", check_components=True, tol=None):
+    from paper_2606_09688_gb300 import Solver
+    jxs, jts = target
+    with Solver(p, precision=precision) as s:
+        info = s.solve(-1)
+        out = s.combine(jxs, jts).cpu().numpy()
+        coeffs = [s.coeffs(k) for k in range(s.num_components)] if check_components else None
+        comps_info = s.components()
+    comps, sols = osolve.solve_all(p, method=method)
+    assert [(c.jx, c.jt, c.coef) for c in comps_info] == comps
+    pts, times = osolve.target_grid(p, jxs, jts)
+    ref = osolve.combine(p, comps, sols, pts, times)
+    tol = tol or (TOL64 if precision == 0 else TOL32)
+    err = _rel(out, ref)
+    assert err < tol, (p.name, err, info.rel_residual)
+    if check_components:
+        for (jx, jt, c), U, Uo in zip(comps, coeffs, sols):
+            if np.linalg.norm(Uo) > 0:
+                assert _rel(U, Uo) < 10 * tol, (jx, jt, _rel(U, Uo))
+    return err, info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_standing_wave_1d_level6(prec):
+    """The 1D configuration: c = 1, f = 0, u0 = sin(pi x), n = 6, m = 1 (9 components)."""
+    p = W.standing_wave(1, 6, 1)
+    _run(p, prec, (5, 5))
+    _run(p, prec, (6, 6))     # target finer than every component
+    _run(p, prec, (3, 2))     # target coarser than most components
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_variable_speed_general_source_1d(prec):
+    """Section 6.2 data: c^2 = 1 + x, u0 and v0 non-zero, non-separable f."""
+    _run(W.e2_variable_speed(4), prec, (5, 5))
+
+
+def test_vanishing_example_1d_domain_minus1_1():
+    _run(W.e1_vanishing(4), 0, (6, 5))
+
+
+def test_space_eigenbasis_components_1d():
+    """n = 11, m = 1: components with 2^jt + 1 > 129 time unknowns use the
+    spatial eigenbasis with banded time solves.  Their systems are
+    ill-conditioned (the oracle's own sparse-LU solution of the (1,10)
+    component leaves a relative residual of 6.6e-10, i.e. cond(S) eps ~ 1e-9),
+    so two correct FP64 solvers agree only to that level: tolerance 2e-9."""
+    _run(W.standing_wave(1, 11, 1), 0, (8, 8), check_components=True, tol=2e-9)
+
+
+def test_single_component_level_zero():
+    p = W.standing_wave(2, 6, 3)
+    err, _ = _run(p, 0, (3, 3))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_standing_wave_2d(prec):
+    _run(W.standing_wave(2, 7, 2), prec, (5, 5))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_layered_medium_2d_multigrid(prec):
+    """The 2D layered medium at n = 8, m = 2: the (6,2) and (5,2) components
+    (more than 1024 spatial unknowns) go through COCG with the multigrid
+    V-cycle; the others are direct."""
+    _run(W.layered_2d(8, 2), prec, (6, 6))
+
+
+def test_layered_medium_2d_level10():
+    """n = 10: (8,2) 255^2 x 5 with a 4-level V-cycle; (2,8) with the space eigenbasis."""
+    _run(W.layered_2d(10, 2), 1, (8, 8), method="schur", check_components=False)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_standing_wave_3d(prec):
+    _run(W.standing_wave(3, 6, 2), prec, (4, 4))
+
+
+def test_random_medium_3d_small():
+    _run(W.random_medium_3d(6, 2, seed=3), 1, (4, 4))
+
+
+def test_errors_are_reported():
+    from paper_2606_09688_gb300 import Solver, StError
+    from paper_2606_09688_gb300 import st as B
+    bad = W.standing_wave(2, 6, 2)
+    bad.c2 = lambda x: -np.ones(len(x))
+    with pytest.raises(StError) as e:
+        Solver(bad)
+    assert e.value.code == B.ST_ERR_ARG
+    boom = W.standing_wave(1, 4, 1)
+
+    def raises(x):
+        raise ValueError("data")
+    boom.u0 = raises
+    with pytest.raises(StError) as e:
+        Solver(boom)
+    assert e.value.code == B.ST_ERR_CALLBACK
+    with Solver(W.standing_wave(1, 4, 1)) as s:
+        with pytest.raises(StError) as e:
+            s.combine(3, 3)
+        assert e.value.code == B.ST_ERR_STATE
+        with pytest.raises(StError) as e:
+            s.solve(99)
+        assert e.value.code == B.ST_ERR_ARG
