@@ -169,6 +169,38 @@ st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n
 st_status st_destroy(st_handle* h);
 const char* st_last_error(const st_handle* h);
 
+/* Allocation-free combination.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let the library allocate device memory
+ * at call time (for instance when another allocator has reserved the device
+ * memory, or inside a time-critical loop where cudaMalloc would synchronise
+ * the device).  It computes the same target-grid values as st_combine from
+ * caller-owned component arrays and writes them to caller-owned out_dev
+ * ((2^jx*+1)^d x (2^jt*+1) doubles, layout as in st_combine).
+ *
+ * comps[k]: U = device array of component k's coefficients (n_time x n_space,
+ * time-major, the layout of st_component_coeffs), lift = device array of u0 on
+ * all (2^jx+1)^d nodes of level jx (NULL if u0 = 0), levels and coefficient.
+ * At most 64 components.
+ *
+ * Scratch: a fixed 32 MiB array in device global memory, part of the library
+ * image, so every GPU that loads the library holds it until the process exits.
+ * Requests whose tables and partial sums do not fit are rejected with
+ * ST_ERR_ARG (so are bad arguments); a failed CUDA call gives ST_ERR_CUDA.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its first call on a device looks up the device address of the
+ * scratch array (with that device current); make that first call before any
+ * stream capture.  Every call reuses the same scratch and overwrites all of
+ * it that it reads, so calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race and must be serialised by the
+ * caller.  Work is enqueued on `stream`; the call does not synchronise. */
+typedef struct {
+  const double* U;
+  const double* lift;
+  int jx, jt, coef;
+} st_comb_input;
+st_status st_combine_noalloc(const st_comb_input* comps, int ncomp, int d, double T, int jx_star, int jt_star,
+                             double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
