@@ -48,7 +48,8 @@ typedef enum {
   ST_ERR_NOT_CONVERGED = 4,  /* an iterative solve hit its iteration limit */
   ST_ERR_STATE = 5,          /* call out of order (e.g. combine before solve) */
   ST_ERR_CALLBACK = 6,       /* a user callback returned non-zero */
-  ST_ERR_NUMERIC = 7         /* NaN/Inf or a breakdown in a factorisation */
+  ST_ERR_NUMERIC = 7,        /* NaN/Inf or a breakdown in a factorisation */
+  ST_ERR_TIMEOUT = 8         /* a bounded wait inside a kernel gave up */
 } st_status;
 
 typedef enum { ST_FP64 = 0, ST_FP32_IR = 1 } st_precision;

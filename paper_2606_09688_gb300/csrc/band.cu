@@ -1,0 +1,330 @@
+// Banded complex-symmetric LDL^T: assembly, factorisation and the solve of
+// the spatial problems (K + lam_q M) x = b on grids small enough for a direct
+// method (whole component grids, or the coarsest multigrid level).
+//
+// Storage (per mode q, at q * mstride): row k of F holds column k of L,
+// F[k][t] = L_{k+t,k} (t = 1..bw) and F[k][0] = d_k; row k of G holds row k of L,
+// G[k][t] = L_{k,k-t}.  Rows are padded to an even length ld so that every
+// row starts on a 16-byte boundary (TMA bulk copies).
+//
+// Solve: one warp per mode.  Forward (L y = b, column-oriented with F rows in
+// increasing k) and backward (L^T x = z, column-oriented with G rows in
+// decreasing k) share one routine: a window of the next bw right-hand-side
+// rows lives in registers (row r in slot r mod bw, lane = slot mod 32), the
+// finished row is broadcast with one shuffle, and every lane updates its
+// slots.  Factor rows are streamed into shared memory in chunks by
+// cp.async.bulk with mbarrier completion, two chunks in flight.
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+
+#include "band.h"
+
+namespace st {
+
+namespace {
+
+constexpr int kBlock = 256;
+inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for a phase of the barrier for at most ~2^31 cycles (about one second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------- assembly
+template <typename R>
+__global__ void k_band_form(const double* __restrict__ Kb, const double* __restrict__ Mb,
+                            const cx<double>* __restrict__ lam, cx<R>* __restrict__ F, BandLayout L) {
+  const int q = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = L.bw + 1;
+  if (e >= L.nrow * L.ld) return;
+  const int64_t k = e / L.ld;
+  const int t = (int)(e - k * L.ld);
+  cx<R> v = mk<R>(0, 0);
+  if (t < W) {
+    const cx<double> l = lam[q];
+    const double kb = Kb[k * W + t], mb = Mb[k * W + t];
+    v = mk<R>((R)(kb + l.re * mb), (R)(l.im * mb));
+  }
+  F[(int64_t)q * L.mstride + e] = v;
+}
+
+// Right-looking LDL^T without pivoting of a complex-symmetric band (see
+// band.h for why no pivot is needed).  One CTA per mode; column k:
+// a_{k+i,k+j} -= a_{k+i,k} a_{k+j,k} / d_k, then l_{k+i,k} = a_{k+i,k} / d_k.
+template <typename R>
+__global__ void k_band_ldlt(cx<R>* __restrict__ F, BandLayout L, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* col = reinterpret_cast<cx<R>*>(smem_raw);
+  const int q = blockIdx.x;
+  const int bw = L.bw, ld = L.ld;
+  const int64_t nrow = L.nrow;
+  cx<R>* Fq = F + (int64_t)q * L.mstride;
+  for (int64_t k = 0; k < nrow; ++k) {
+    __syncthreads();
+    for (int t = threadIdx.x; t <= bw; t += blockDim.x) col[t] = (k + t < nrow) ? Fq[k * ld + t] : mk<R>(0, 0);
+    __syncthreads();
+    const cx<R> d = col[0];
+    if (!(d.re * d.re + d.im * d.im > R(0))) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      return;
+    }
+    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
+    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
+    // pairs (ii, jj) with 1 <= jj <= ii <= m, enumerated row by row of the lower triangle
+    const int npairs = m * (m + 1) / 2;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+      int ii = (int)((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
+      while (ii * (ii + 1) / 2 > p) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
+      const int jj = p - ii * (ii + 1) / 2;  // 0 <= jj <= ii
+      const int i1 = ii + 1, j1 = jj + 1;
+      cx<R>& tgt = Fq[(k + j1) * ld + (i1 - j1)];
+      tgt = tgt - (col[i1] * col[j1]) * dinv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x + 1; t <= m; t += blockDim.x) Fq[k * ld + t] = col[t] * dinv;
+  }
+}
+
+template <typename R>
+__global__ void k_band_rows(const cx<R>* __restrict__ F, cx<R>* __restrict__ G, BandLayout L) {
+  const int q = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L.nrow * L.ld) return;
+  const int64_t k = e / L.ld;
+  const int t = (int)(e - k * L.ld);
+  cx<R> v = mk<R>(0, 0);
+  if (t == 0) v = F[(int64_t)q * L.mstride + k * L.ld];
+  else if (t <= L.bw && k - t >= 0) v = F[(int64_t)q * L.mstride + (k - t) * L.ld + t];
+  G[(int64_t)q * L.mstride + e] = v;
+}
+
+// ----------------------------------------------------------------- solve
+template <typename R, int SLOTS>
+__global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F, const cx<R>* __restrict__ G,
+                                                     BandLayout L, int C, const cx<R>* __restrict__ b,
+                                                     cx<R>* __restrict__ x, const CocgScal* __restrict__ scal,
+                                                     int64_t vstride, int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = blockIdx.x;
+  if (scal != nullptr && !scal[q].active) return;
+  const int lane = threadIdx.x;
+  const int bw = L.bw, ld = L.ld, nrow = (int)L.nrow;
+  const size_t stage_elems = (size_t)C * ld;
+  cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem);
+  cx<R>* stage1 = stage0 + stage_elems;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage1 + stage_elems);
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  unsigned phase[2] = {0u, 0u};
+  const int nchunks = (nrow + C - 1) / C;
+  cx<R>* dst = x + (int64_t)q * vstride;
+  for (int pass = 0; pass < 2; ++pass) {
+    const cx<R>* Mq = (pass == 0 ? F : G) + (int64_t)q * L.mstride;
+    const cx<R>* src = pass == 0 ? b + (int64_t)q * vstride : dst;
+    // chunk c holds the pass-order rows c*C .. c*C+cnt-1; in memory they are
+    // rows klo .. klo+cnt-1 (increasing), i.e. reversed for the backward pass
+    auto chunk = [&](int c, int& klo, int& cnt) {
+      const int k0 = c * C;
+      cnt = min(C, nrow - k0);
+      klo = pass == 0 ? k0 : nrow - k0 - cnt;
+    };
+    auto issue = [&](int c) {
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      cx<R>* st = (c & 1) ? stage1 : stage0;
+      const unsigned bytes = (unsigned)((size_t)cnt * ld * sizeof(cx<R>));
+      mbar_expect_tx(&bar[c & 1], bytes);
+      bulk_g2s(st, Mq + (int64_t)klo * ld, bytes, &bar[c & 1]);
+    };
+    if (lane == 0) {
+      issue(0);
+      if (nchunks > 1) issue(1);
+    }
+    auto at = [&](int rp) -> cx<R> {  // right-hand side of pass-order row rp
+      const int r = pass == 0 ? rp : nrow - 1 - rp;
+      return src[r];
+    };
+    cx<R> v[SLOTS], nb[SLOTS];
+    int tc[SLOTS];
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      const int j = lane + 32 * s;
+      v[s] = (j < bw && j < nrow) ? at(j) : mk<R>(0, 0);
+      nb[s] = (j < bw && j + bw < nrow) ? at(j + bw) : mk<R>(0, 0);
+      tc[s] = j;
+    }
+    int jk = 0;  // slot of the row finished at this step (pass-order row mod bw)
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      phase[c & 1] ^= 1u;
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      const cx<R>* st = (c & 1) ? stage1 : stage0;
+      for (int i = 0; i < cnt; ++i) {
+        const int kp = c * C + i;
+        const int k = pass == 0 ? kp : nrow - 1 - kp;
+        const cx<R>* row = st + (size_t)(k - klo) * ld;
+        cx<R> mine = v[0];
+#pragma unroll
+        for (int s = 1; s < SLOTS; ++s)
+          if (tc[s] == 0) mine = v[s];
+        const int owner = jk & 31;
+        cx<R> y;
+        y.re = __shfl_sync(0xffffffffu, mine.re, owner);
+        y.im = __shfl_sync(0xffffffffu, mine.im, owner);
+        if (lane == owner) dst[k] = pass == 0 ? cdiv(y, row[0]) : y;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          const int j = lane + 32 * s;
+          if (j >= bw) continue;
+          int t = tc[s];
+          if (t == 0) {  // this slot takes pass-order row kp + bw
+            t = bw;
+            v[s] = nb[s];
+            const int rn = kp + 2 * bw;
+            nb[s] = rn < nrow ? at(rn) : mk<R>(0, 0);
+            tc[s] = bw - 1;
+          } else {
+            tc[s] = t - 1;
+          }
+          if (kp + t < nrow) {
+            const cx<R> a = row[t];
+            v[s] = mk<R>(v[s].re - (a.re * y.re - a.im * y.im), v[s].im - (a.re * y.im + a.im * y.re));
+          }
+        }
+        jk = (jk + 1 == bw) ? 0 : jk + 1;
+      }
+      __syncwarp();
+      if (lane == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    if (!ok) {
+      // give the copies still in flight a bounded chance to land, then report
+      if (lane == 0) {
+        atomicExch(err, 2);
+        for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
+      }
+      return;
+    }
+    __syncwarp();
+  }
+}
+
+std::mutex g_attr_mu;  // launches come from several host threads (one per component)
+
+template <typename R, int SLOTS> void set_smem_attr(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_solve_w<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
+}  // namespace
+
+BandLayout band_layout(int64_t nrow, int bw) {
+  BandLayout L;
+  L.nrow = nrow;
+  L.bw = bw;
+  L.ld = (bw + 1 + 1) & ~1;
+  L.mstride = ((nrow * L.ld + 2 + 31) / 32) * 32;
+  return L;
+}
+
+template <typename R>
+void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, const BandLayout& L,
+                      int nmodes, cudaStream_t s) {
+  k_band_form<R><<<dim3(blocks_for(L.nrow * L.ld), nmodes), kBlock, 0, s>>>(Kb, Mb, lam, F, L);
+  note_launches(1);
+}
+
+template <typename R>
+void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int* err, cudaStream_t s) {
+  k_band_ldlt<R><<<nmodes, 256, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, err);
+  k_band_rows<R><<<dim3(blocks_for(L.nrow * L.ld), nmodes), kBlock, 0, s>>>(F, G, L);
+  note_launches(2);
+}
+
+int band_chunk_rows(const BandLayout& L, size_t elem) {
+  int C = (int)(32768 / (L.ld * elem));
+  C = C < 2 ? 2 : (C > 64 ? 64 : C);
+  return C & ~1;
+}
+
+template <typename R>
+bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, const cx<R>* b, cx<R>* x,
+                       const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s) {
+  const int C = band_chunk_rows(L, sizeof(cx<R>));
+  const size_t smem = 2 * (size_t)C * L.ld * sizeof(cx<R>) + 2 * sizeof(uint64_t);
+  if (L.bw <= 32) {
+    set_smem_attr<R, 1>(smem);
+    k_band_solve_w<R, 1><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else if (L.bw <= 64) {
+    set_smem_attr<R, 2>(smem);
+    k_band_solve_w<R, 2><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else if (L.bw <= 128) {
+    set_smem_attr<R, 4>(smem);
+    k_band_solve_w<R, 4><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else if (L.bw <= 256) {
+    set_smem_attr<R, 8>(smem);
+    k_band_solve_w<R, 8><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else {
+    return false;
+  }
+  note_launches(1);
+  return true;
+}
+
+#define ST_BAND_INST(R)                                                                                              \
+  template void launch_band_form<R>(const double*, const double*, const cx<double>*, cx<R>*, const BandLayout&, int, \
+                                    cudaStream_t);                                                                   \
+  template void launch_band_factor<R>(cx<R>*, cx<R>*, const BandLayout&, int, int*, cudaStream_t);                  \
+  template bool launch_band_solve<R>(const cx<R>*, const cx<R>*, const BandLayout&, const cx<R>*, cx<R>*,           \
+                                     const CocgScal*, int, int64_t, int*, cudaStream_t);
+ST_BAND_INST(double)
+ST_BAND_INST(float)
+#undef ST_BAND_INST
+
+}  // namespace st

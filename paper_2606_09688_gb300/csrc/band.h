@@ -1,0 +1,40 @@
+// Banded complex-symmetric LDL^T of K + lam M (see band.cu).
+//
+// No pivoting is needed: for Im lam != 0 the matrix -i (K + lam M) has the
+// positive definite Hermitian part Im(lam) M, and for real lam > 0 the matrix
+// K + lam M is symmetric positive definite, so every leading principal minor
+// is non-singular.  The eigenvalues of B^{-1} A are either non-real or real
+// and positive (checked in setup).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace st {
+
+struct BandLayout {
+  int64_t nrow;     // unknowns of the grid
+  int bw;           // half bandwidth: 1 (1D), n+1 (2D), n^2+n+1 (3D)
+  int ld;           // row length in elements: bw + 1 rounded up to even
+  int64_t mstride;  // elements per mode (multiple of 32)
+};
+
+BandLayout band_layout(int64_t nrow, int bw);
+int band_chunk_rows(const BandLayout& L, size_t elem);
+
+template <typename R>
+void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, const BandLayout& L,
+                      int nmodes, cudaStream_t s);
+// LDL^T of every mode's F in place, then G (rows of L) from F.  err[0] = 1 on a zero pivot.
+template <typename R>
+void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int* err, cudaStream_t s);
+// x_q = (L D L^T)^{-1} b_q for every active mode (vectors at q * vstride);
+// x may alias nothing but itself.  err[0] = 2 if a copy wait timed out.
+// Returns false when bw exceeds 256 (not supported).
+template <typename R>
+bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, const cx<R>* b, cx<R>* x,
+                       const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s);
+
+}  // namespace st

@@ -31,6 +31,22 @@ template <typename R> __host__ __device__ __forceinline__ cx<R> fma_c(cx<R> c, c
   return {fma(c.re, b.re, fma(-c.im, b.im, a.re)), fma(c.re, b.im, fma(c.im, b.re, a.im))};
 }
 
+// Division of a 32-bit unsigned a < 2^31 by a fixed divisor d >= 1 with one
+// high multiply (Granlund and Montgomery, 1994): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, a / d = (umulhi(a, m) + a) >> l.
+struct FastDiv {
+  unsigned d, m, l;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (unsigned)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1ull);
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned a, const FastDiv& f) { return (__umulhi(a, f.m) + a) >> f.l; }
+
 // Uniform tensor grid of one spatial level: N = 2^j cells per direction, the
 // interior nodes (Dirichlet unknowns) number n = N - 1 per direction and are
 // ordered lexicographically with the first coordinate fastest.
@@ -40,6 +56,7 @@ struct Geo {
   int n;              // interior nodes per direction
   int64_t nnodes;     // n^d
   int64_t ncells;     // N^d
+  FastDiv dn;         // division by n
 };
 
 // Q1 stencil of a node with its 3^d neighbours (offset delta in {-1,0,1}^d,

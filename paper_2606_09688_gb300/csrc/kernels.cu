@@ -21,10 +21,16 @@ inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n +
 std::atomic<int64_t> g_launches{0};
 inline void count(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-template <int D> __device__ __forceinline__ void decode(int64_t a, int n, int i[3]) {
-  i[0] = (int)(a % n);
-  if (D > 1) i[1] = (int)((a / n) % n);
-  if (D > 2) i[2] = (int)(a / ((int64_t)n * n));
+// Interior node index -> coordinates (node counts stay below 2^31).
+template <int D> __device__ __forceinline__ void decode(int64_t a64, const Geo& g, int i[3]) {
+  const unsigned a = (unsigned)a64;
+  const unsigned q1 = fdiv(a, g.dn);
+  i[0] = (int)(a - q1 * (unsigned)g.n);
+  if (D > 1) {
+    const unsigned q2 = fdiv(q1, g.dn);
+    i[1] = (int)(q1 - q2 * (unsigned)g.n);
+    if (D > 2) i[2] = (int)q2;
+  }
 }
 
 // Sums of c^2 over the cells shared by a node and each of its 3^D neighbours.
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const
   if (a >= g.nnodes) return;
   constexpr int NS = ipow3(D), CEN = (NS - 1) / 2;
   int i[3] = {0, 0, 0};
-  decode<D>(a, g.n, i);
+  decode<D>(a, g, i);
   R S[NS];
   cell_sums<D, R>(c2, g.N, i, S);
   const cx<R> l = lam[q];
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict(Geo gf, Geo gc, const cx<R>
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= gc.nnodes) return;
   int ic[3] = {0, 0, 0};
-  decode<D>(I, gc.n, ic);
+  decode<D>(I, gc, ic);
   constexpr int NS = ipow3(D);
   cx<R> acc = mk<R>(0, 0);
 #pragma unroll
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, const cx
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= gf.nnodes) return;
   int i[3] = {0, 0, 0};
-  decode<D>(a, gf.n, i);
+  decode<D>(a, gf, i);
   cx<R> acc = mk<R>(0, 0);
 #pragma unroll
   for (int e = 0; e < (1 << D); ++e) {
@@ -209,79 +215,6 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, const cx
     if (ok) acc = fma_s(w, xc[(int64_t)q * scs + idx], acc);
   }
   xf[(int64_t)q * sf + a] = xf[(int64_t)q * sf + a] + acc;
-}
-
-// ------------------------------------------------------------ band LDL^T
-template <typename R>
-__global__ void k_band_form(const double* __restrict__ Kb, const double* __restrict__ Mb,
-                            const cx<double>* __restrict__ lam, cx<R>* __restrict__ F, int64_t total) {
-  const int q = blockIdx.y;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const cx<double> l = lam[q];
-  F[(int64_t)q * total + e] = mk<R>((R)(Kb[e] + l.re * Mb[e]), (R)(l.im * Mb[e]));
-}
-
-// Right-looking LDL^T without pivoting of a complex-symmetric band matrix
-// (symmetric part of -i(K + lam M) is Im(lam) M, positive definite when
-// Im lam > 0, and K + lam M is SPD for real lam > 0, so every leading minor is
-// non-singular).  Column k: d_k = a_kk; a_{k+i,k+j} -= a_{k+i,k} a_{k+j,k} / d_k;
-// l_{k+i,k} = a_{k+i,k} / d_k.  One CTA per mode.
-template <typename R>
-__global__ void k_band_ldlt(cx<R>* __restrict__ F, int64_t nrow, int bw, int* err) {
-  extern __shared__ unsigned char smem_raw[];
-  cx<R>* col = reinterpret_cast<cx<R>*>(smem_raw);
-  const int q = blockIdx.x;
-  const int W = bw + 1;
-  cx<R>* Fq = F + (int64_t)q * nrow * W;
-  for (int64_t k = 0; k < nrow; ++k) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < W; t += blockDim.x) col[t] = (k + t < nrow) ? Fq[k * W + t] : mk<R>(0, 0);
-    __syncthreads();
-    const cx<R> d = col[0];
-    if (!(d.re * d.re + d.im * d.im > R(0))) {
-      if (threadIdx.x == 0) atomicExch(err, 1);
-      return;
-    }
-    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
-    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
-    for (int p = threadIdx.x; p < m * m; p += blockDim.x) {
-      const int ii = p / m + 1, jj = p % m + 1;
-      if (jj > ii) continue;
-      cx<R>& tgt = Fq[(k + jj) * W + (ii - jj)];
-      tgt = tgt - (col[ii] * col[jj]) * dinv;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x + 1; t <= m; t += blockDim.x) Fq[k * W + t] = col[t] * dinv;
-  }
-}
-
-// x = (L D L^T)^{-1} b for one mode per CTA; the whole vector lives in shared memory.
-template <typename R>
-__global__ void k_band_solve(const cx<R>* __restrict__ F, int64_t nrow, int bw, const cx<R>* __restrict__ b,
-                             cx<R>* __restrict__ x, const CocgScal* __restrict__ scal, int64_t stride) {
-  extern __shared__ unsigned char smem_raw[];
-  cx<R>* v = reinterpret_cast<cx<R>*>(smem_raw);
-  const int q = blockIdx.x;
-  if (scal != nullptr && !scal[q].active) return;
-  const int W = bw + 1;
-  const cx<R>* Fq = F + (int64_t)q * nrow * W;
-  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) v[k] = b[(int64_t)q * stride + k];
-  __syncthreads();
-  for (int64_t k = 0; k < nrow; ++k) {
-    const cx<R> yk = v[k];
-    for (int t = threadIdx.x + 1; t <= bw && k + t < nrow; t += blockDim.x) v[k + t] = v[k + t] - Fq[k * W + t] * yk;
-    __syncthreads();
-  }
-  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) v[k] = cdiv(v[k], Fq[k * W]);
-  __syncthreads();
-  for (int64_t k = nrow - 1; k >= 0; --k) {
-    const cx<R> xk = v[k];
-    for (int t = threadIdx.x + 1; t <= bw && k - t >= 0; t += blockDim.x)
-      v[k - t] = v[k - t] - Fq[(k - t) * W + t] * xk;
-    __syncthreads();
-  }
-  for (int64_t k = threadIdx.x; k < nrow; k += blockDim.x) x[(int64_t)q * stride + k] = v[k];
 }
 
 // ------------------------------------------------------------ COCG pieces
@@ -521,7 +454,7 @@ __global__ void __launch_bounds__(kBlock) k_stencil_real2(Geo g, StencilCoef sc,
   if (a >= g.nnodes) return;
   constexpr int NS = ipow3(D);
   int i[3] = {0, 0, 0};
-  decode<D>(a, g.n, i);
+  decode<D>(a, g, i);
   double S[NS];
   cell_sums<D, double>(c2, g.N, i, S);
   const double* xr = x + (int64_t)row * xrow;
@@ -664,7 +597,7 @@ template <int D>
 __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __restrict__ Yprev,
                                                        const CombComp* __restrict__ comps, int c0, int c1,
                                                        const double* __restrict__ tbv, const int* __restrict__ tspan,
-                                                       int nts, double* __restrict__ Y) {
+                                                       int nts, double* __restrict__ Y, FastDiv dN1) {
   const int s = blockIdx.y;
   const int Nj = 1 << j;
   int64_t nsp = 1;
@@ -674,11 +607,12 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
   if (p >= nsp) return;
   int P[3] = {0, 0, 0};
   {
-    int64_t r = p;
+    unsigned r = (unsigned)p;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      P[k] = (int)(r % (Nj + 1));
-      r /= (Nj + 1);
+      const unsigned qq = fdiv(r, dN1);
+      P[k] = (int)(r - qq * (unsigned)(Nj + 1));
+      r = qq;
     }
   }
   double v = 0.0;
@@ -782,35 +716,6 @@ void launch_prolong_add(const Geo& gf, const Geo& gc, const cx<R>* xc, cx<R>* xf
   if (gf.d == 1) k_prolong_add<1, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
   else if (gf.d == 2) k_prolong_add<2, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
   else k_prolong_add<3, R><<<grid, kBlock, 0, s>>>(gf, gc, xc, xf, scal, sf, scs);
-}
-
-template <typename R>
-void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, int64_t nrow, int bw,
-                      int nmodes, cudaStream_t s) {
-  count(1);
-  const int64_t total = nrow * (bw + 1);
-  k_band_form<R><<<dim3(blocks_for(total), nmodes), kBlock, 0, s>>>(Kb, Mb, lam, F, total);
-}
-
-template <typename R>
-void launch_band_ldlt(cx<R>* F, int64_t nrow, int bw, int nmodes, int* err, cudaStream_t s) {
-  count(1);
-  k_band_ldlt<R><<<nmodes, 256, (bw + 1) * sizeof(cx<R>), s>>>(F, nrow, bw, err);
-}
-
-template <typename R>
-void launch_band_solve(const cx<R>* F, int64_t nrow, int bw, const cx<R>* b, cx<R>* x, const CocgScal* scal,
-                       int nmodes, int64_t stride, cudaStream_t s) {
-  count(1);
-  int threads = ((bw + 31) / 32) * 32;
-  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
-  const size_t smem = (size_t)nrow * sizeof(cx<R>);
-  static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once per type
-  if (!attr) {
-    cudaFuncSetAttribute(k_band_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
-  }
-  k_band_solve<R><<<nmodes, threads, smem, s>>>(F, nrow, bw, b, x, scal, stride);
 }
 
 template <typename R>
@@ -918,12 +823,14 @@ void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps,
   int64_t nsp = 1;
   for (int k = 0; k < d; ++k) nsp *= ((1 << j) + 1);
   dim3 grid(blocks_for(nsp), nts);
-  if (d == 1) k_comb_level<1><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
-  else if (d == 2) k_comb_level<2><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
-  else k_comb_level<3><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y);
+  const FastDiv f = make_fastdiv((unsigned)((1 << j) + 1));
+  if (d == 1) k_comb_level<1><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
+  else if (d == 2) k_comb_level<2><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
+  else k_comb_level<3><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
 }
 
 int64_t kernel_launch_count() { return g_launches.load(); }
+void note_launches(int k) { count(k); }
 
 // explicit instantiations
 #define ST_INST(R)                                                                                                   \
@@ -933,11 +840,6 @@ int64_t kernel_launch_count() { return g_launches.load(); }
                                    int64_t, cudaStream_t);                                                           \
   template void launch_prolong_add<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,   \
                                       int64_t, cudaStream_t);                                                        \
-  template void launch_band_form<R>(const double*, const double*, const cx<double>*, cx<R>*, int64_t, int, int,      \
-                                    cudaStream_t);                                                                   \
-  template void launch_band_ldlt<R>(cx<R>*, int64_t, int, int, int*, cudaStream_t);                                 \
-  template void launch_band_solve<R>(const cx<R>*, int64_t, int, const cx<R>*, cx<R>*, const CocgScal*, int,         \
-                                     int64_t, cudaStream_t);                                                         \
   template void launch_cocg_init<R>(const cx<R>*, cx<R>*, cx<R>*, CocgScal*, double*, int, int64_t, int64_t,         \
                                     cudaStream_t);                                                                   \
   template void launch_dot<R>(int, const cx<R>*, const cx<R>*, CocgScal*, double*, int, int64_t, int64_t, double,    \

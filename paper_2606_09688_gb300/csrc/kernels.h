@@ -32,17 +32,6 @@ template <typename R>
 void launch_prolong_add(const Geo& gf, const Geo& gc, const cx<R>* xc, cx<R>* xf, const CocgScal* scal, int nmodes,
                         int64_t sf, int64_t scs, cudaStream_t s);
 
-// Banded complex-symmetric LDL^T (lower band b, column storage F[q][k][j] =
-// entry (k+j, k)): form K + lam_q M from the real bands, factorise, solve.
-template <typename R>
-void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam, cx<R>* F, int64_t nrow, int bw,
-                      int nmodes, cudaStream_t s);
-template <typename R>
-void launch_band_ldlt(cx<R>* F, int64_t nrow, int bw, int nmodes, int* err, cudaStream_t s);
-template <typename R>
-void launch_band_solve(const cx<R>* F, int64_t nrow, int bw, const cx<R>* b, cx<R>* x, const CocgScal* scal,
-                       int nmodes, int64_t stride, cudaStream_t s);
-
 // COCG vector steps with deterministic two-pass reductions.
 template <typename R>
 void launch_cocg_init(const cx<R>* b, cx<R>* x, cx<R>* r, CocgScal* scal, double* part, int nmodes, int64_t n,
@@ -104,5 +93,6 @@ void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps,
 
 // Kernels launched by this process through the wrappers above.
 int64_t kernel_launch_count();
+void note_launches(int k);
 
 }  // namespace st

@@ -20,11 +20,14 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
 #include "../../include/st.h"
 #include "../../include/st_host.h"
+#include "band.h"
 #include "host_math.h"
 #include "kernels.h"
 
@@ -32,7 +35,8 @@ using namespace st;
 
 namespace {
 
-constexpr int kMaxDirectRows = 4096;   // banded direct solves keep the vector in shared memory
+constexpr int kMaxDirectRows = 16384;  // largest grid solved by the banded direct method
+constexpr int kMaxBandWidth = 256;     // widest band the warp solve supports
 constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
 constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
 constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64
@@ -93,6 +97,7 @@ Geo make_geo(int d, int j) {
     g.nnodes *= g.n;
     g.ncells *= g.N;
   }
+  g.dn = make_fastdiv((unsigned)g.n);
   return g;
 }
 
@@ -151,7 +156,8 @@ template <typename R> struct Work {
   cx<R>* T0 = nullptr;
   cx<R>* R0 = nullptr;
   std::vector<cx<R>*> bl, rl, xa, xb;  // per MG level l >= 1
-  cx<R>* band = nullptr;               // nsel x nrow x (bw + 1)
+  cx<R>* band = nullptr;               // F factors, nsel x mstride
+  cx<R>* bandG = nullptr;              // G (rows of L), nsel x mstride
   bool ready = false;
 };
 
@@ -178,6 +184,7 @@ struct Component {
   std::vector<MGLevel> mg;  // mg[0] = component level
   int64_t nrowc = 0;
   int bw = 0;
+  BandLayout bl{};
   std::vector<double> Kband, Mband;
   double* Kb = nullptr;
   double* Mb = nullptr;
@@ -195,6 +202,16 @@ struct Component {
   double Snorm = 0.0;  // upper bound of ||A (x) M + B (x) K||_2
   st_solve_info info{};
   int nactive = 0;  // modes still iterating at the last host check (for byte accounting)
+  // Execution context: every component runs on its own stream with its own
+  // reduction scratch, so that independent components overlap on the GPU.
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done = nullptr;
+  double* cpart = nullptr;
+  double* cscalar = nullptr;
+  double* cscalar_h = nullptr;  // pinned
+  int* cerr = nullptr;
+  int64_t d2h = 0;
+  std::string err;
 };
 
 // Algorithmic flops per node of the complex Q1 stencil (K and M parts with
@@ -218,6 +235,8 @@ struct st_handle {
   int64_t launches0 = 0;
   std::string err;
   int* dev_err = nullptr;
+  int* solve_err = nullptr;  // set by bounded waits inside the band solve
+  cudaEvent_t entry_ev = nullptr;
   struct CombTables {
     CombComp* comps = nullptr;  // components ordered by combination level
     double* tb = nullptr;
@@ -236,6 +255,7 @@ struct st_handle {
     double bytes, flops;
   };
   bool prof_on = false;
+  std::mutex prof_mu;
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t get_event() {
@@ -251,6 +271,12 @@ struct st_handle {
 
   ~st_handle() {
     if (scalar_h) cudaFreeHost(scalar_h);
+    for (auto& c : comps) {
+      if (c->cscalar_h) cudaFreeHost(c->cscalar_h);
+      if (c->cs) cudaStreamDestroy(c->cs);
+      if (c->done) cudaEventDestroy(c->done);
+    }
+    if (entry_ev) cudaEventDestroy(entry_ev);
     for (auto& r : prof) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -259,6 +285,7 @@ struct st_handle {
   }
 
   template <typename T> T* alloc(size_t n) {
+    std::lock_guard<std::mutex> lock(alloc_mu);
     void* p = nullptr;
     if (n == 0) n = 1;
     if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
@@ -278,6 +305,7 @@ struct st_handle {
     return p;
   }
   int64_t h2d_bytes = 0, d2h_bytes = 0;
+  std::mutex alloc_mu;
 };
 
 namespace {
@@ -312,27 +340,31 @@ const char* const kClassName[KC_COUNT] = {"stencil_apply", "jacobi_smooth", "mg_
 
 struct ProfScope {
   st_handle* h;
+  cudaStream_t s;
   int cls;
   double bytes, flops;
   cudaEvent_t a = nullptr;
-  ProfScope(st_handle* h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+  ProfScope(st_handle* h_, cudaStream_t s_, int cls_, double bytes_, double flops_)
+      : h(h_), s(s_), cls(cls_), bytes(bytes_), flops(flops_) {
     if (h->prof_on) {
+      std::lock_guard<std::mutex> lock(h->prof_mu);
       a = h->get_event();
-      cudaEventRecord(a, h->stream);
+      cudaEventRecord(a, s);
     }
   }
   ~ProfScope() {
     if (a) {
+      std::lock_guard<std::mutex> lock(h->prof_mu);
       cudaEvent_t b = h->get_event();
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, s);
       h->prof.push_back({cls, a, b, bytes, flops});
     }
   }
 };
-#define PROF(h, cls, bytes, flops, call) \
-  do {                                  \
-    ProfScope ps_(h, cls, bytes, flops); \
-    call;                               \
+#define PROF(h, s, cls, bytes, flops, call) \
+  do {                                     \
+    ProfScope ps_(h, s, cls, bytes, flops); \
+    call;                                  \
   } while (0)
 
 st_status check_launch(st_handle* h, const char* where) {
@@ -556,8 +588,6 @@ st_status setup_time_level(st_handle* h, int jt, TimeData& td) {
 // modes (k h_c <= theta); grids with at most kMaxDirectRows unknowns are
 // solved directly.
 int choose_coarse(const st_problem& p, const Component& c) {
-  const int64_t nx = make_geo(p.d, c.jx).nnodes;
-  if (nx <= 1024) return c.jx;
   double kmax = 0.0;
   for (int q = 0; q < c.td->eig.nsel; ++q)
     kmax = std::max(kmax, std::sqrt(std::max(0.0, -c.td->eig.lam[q].real()) / c.sl->c2min));
@@ -565,9 +595,14 @@ int choose_coarse(const st_problem& p, const Component& c) {
   for (int k = 0; k < p.d; ++k) L = std::max(L, p.hi[k] - p.lo[k]);
   int jc = 2;
   while (jc < c.jx && kmax * L / (1 << jc) > kThetaMG) ++jc;
-  int jmax = 1;  // largest level whose banded solve fits in shared memory
-  while (jmax + 1 <= c.jx && make_geo(p.d, jmax + 1).nnodes <= kMaxDirectRows) ++jmax;
-  if (jc >= c.jx) return nx <= kMaxDirectRows ? c.jx : jmax;
+  auto fits = [&](int j) {
+    const Geo g = make_geo(p.d, j);
+    return g.nnodes <= kMaxDirectRows && band_width(g) <= kMaxBandWidth;
+  };
+  if (fits(c.jx)) return c.jx;  // the banded direct solve beats a V-cycle with a large coarse grid
+  int jmax = 1;                 // largest level the banded solve handles
+  while (jmax + 1 <= c.jx && fits(jmax + 1)) ++jmax;
+  if (jc >= c.jx) return jmax;
   return std::min(jc, jmax);
 }
 
@@ -722,6 +757,7 @@ st_status setup_component(st_handle* h, Component& c) {
   const MGLevel& lc = c.mg.back();
   c.bw = (int)band_width(lc.geo);
   c.nrowc = lc.geo.nnodes;
+  c.bl = band_layout(c.nrowc, c.bw);
   assemble_band(lc.geo, lc.sc, lc.c2h, c.Kband, c.Mband, c.bw);
   c.Kb = h->upload(c.Kband);
   c.Mb = h->upload(c.Mband);
@@ -742,6 +778,25 @@ template <typename R> const R* c2_of(const MGLevel& l);
 template <> const double* c2_of<double>(const MGLevel& l) { return l.c2d; }
 template <> const float* c2_of<float>(const MGLevel& l) { return l.c2f; }
 
+st_status cfail(Component& c, st_status code, const std::string& msg) {
+  if (c.err.empty()) c.err = msg;
+  return code;
+}
+
+#define ST_CUDAC(c, call)                                                                                 \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess) return cfail(c, ST_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+st_status ccheck(Component& c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cfail(c, ST_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return ST_OK;
+}
+
+// Workspace and coarsest-level factorisations of a time-eigenbasis component
+// (setup time, on the handle's stream).
 template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   Work<R>& w = work_of<R>(c);
   if (w.ready) return ST_OK;
@@ -781,12 +836,13 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
     }
   }
   // coarsest-level factorisations, one per mode
-  w.band = h->alloc<cx<R>>((size_t)c.nsel * c.nrowc * (c.bw + 1));
+  w.band = h->alloc<cx<R>>((size_t)c.nsel * c.bl.mstride);
+  w.bandG = h->alloc<cx<R>>((size_t)c.nsel * c.bl.mstride);
   ST_NEED(h, w.band);
-  const cx<double>* lam64 = c.td->lam64;
-  launch_band_form<R>(c.Kb, c.Mb, lam64, w.band, c.nrowc, c.bw, c.nsel, h->stream);
+  ST_NEED(h, w.bandG);
+  launch_band_form<R>(c.Kb, c.Mb, c.td->lam64, w.band, c.bl, c.nsel, h->stream);
   ST_CUDA(h, cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
-  launch_band_ldlt<R>(w.band, c.nrowc, c.bw, c.nsel, h->dev_err, h->stream);
+  launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, h->dev_err, h->stream);
   int herr = 0;
   ST_CUDA(h, cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -811,34 +867,34 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const MGLevel& lv = c.mg[l];
   const cx<R>* lam = lam_of<R>(*c.td);
   const int64_t n = lv.geo.nnodes;
-  cudaStream_t s = h->stream;
+  cudaStream_t s = c.cs;
   const int L = (int)c.mg.size() - 1;
   const double m = (double)c.nactive, cs = sizeof(cx<R>), rs = sizeof(R);
   const double fl = stencil_flops(lv.geo.d);
   if (l == L) {
-    PROF(h, KC_BAND_SOLVE, m * (double)n * ((c.bw + 1) * cs + 2 * cs), m * (double)n * c.bw * 16.0,
-         launch_band_solve<R>(w.band, c.nrowc, c.bw, b, xb, c.scal, c.nsel, n, s));
+    PROF(h, s, KC_BAND_SOLVE, m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
+         launch_band_solve<R>(w.band, w.bandG, c.bl, b, xb, c.scal, c.nsel, n, c.cerr, s));
     return xb;
   }
   const double om = omega_of(lv.geo.d);
   const R* c2 = c2_of<R>(lv);
   const double cb = (double)lv.geo.ncells * rs;
-  PROF(h, KC_JACOBI, m * n * 2 * cs + cb, m * n * 30.0,
+  PROF(h, s, KC_JACOBI, m * n * 2 * cs + cb, m * n * 30.0,
        launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, lv.sc, c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, KC_MG_RESID, m * n * 3 * cs + cb, m * n * (fl + 2.0),
+  PROF(h, s, KC_MG_RESID, m * n * 3 * cs + cb, m * n * (fl + 2.0),
        launch_stencil<R>(OP_RESID, lv.geo, lv.sc, c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
   const MGLevel& lc = c.mg[l + 1];
   const double nc = (double)lc.geo.nnodes;
-  PROF(h, KC_RESTRICT, m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
+  PROF(h, s, KC_RESTRICT, m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
        launch_restrict<R>(lv.geo, lc.geo, rtmp, w.bl[l + 1], c.scal, c.nsel, n, lc.geo.nnodes, s));
   cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
-  PROF(h, KC_PROLONG, m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
+  PROF(h, s, KC_PROLONG, m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
        launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
-  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
   return xb;
 }
@@ -846,16 +902,16 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
 // Solve (lam_q M + K) x_q = g_q for every mode; w.G holds g, the result lands in w.X.
 template <typename R> st_status inner_solve(st_handle* h, Component& c, int& iters_out) {
   Work<R>& w = work_of<R>(c);
-  cudaStream_t s = h->stream;
+  cudaStream_t s = c.cs;
   const int64_t n = c.nx;
   const double cs = sizeof(cx<R>), rs = sizeof(R);
   iters_out = 0;
   c.nactive = c.nsel;
   if (c.direct) {
     const double m = c.nsel;
-    PROF(h, KC_BAND_SOLVE, m * (double)n * ((c.bw + 1) * cs + 2 * cs), m * (double)n * c.bw * 16.0,
-         launch_band_solve<R>(w.band, c.nrowc, c.bw, w.G, w.X, nullptr, c.nsel, n, s));
-    return check_launch(h, "direct band solve");
+    PROF(h, s, KC_BAND_SOLVE, m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
+         launch_band_solve<R>(w.band, w.bandG, c.bl, w.G, w.X, nullptr, c.nsel, n, c.cerr, s));
+    return ccheck(c, "direct band solve");
   }
   const double tol = sizeof(R) == 8 ? 1e-12 : 1e-5;
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
@@ -863,28 +919,27 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
   const R* c2 = c2_of<R>(l0);
   const cx<R>* lam = lam_of<R>(*c.td);
   const double fl = stencil_flops(l0.geo.d), cb = (double)l0.geo.ncells * rs;
-  PROF(h, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
+  PROF(h, s, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
        launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
   // z = B r ; rho = r . z ; p = z
   cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-  PROF(h, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
+  PROF(h, s, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
        launch_dot<R>(2, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-  PROF(h, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0,
-       launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
+  PROF(h, s, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
   const int check_every = 4;
   for (int it = 1; it <= max_iter; ++it) {
     const double m = c.nactive;
-    PROF(h, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
+    PROF(h, s, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
          launch_stencil<R>(OP_APPLY, l0.geo, l0.sc, c2, w.P, nullptr, w.Wv, lam, c.scal, c.nsel, n, 0.0, s));
-    PROF(h, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+    PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
          launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-    PROF(h, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
+    PROF(h, s, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
          launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
     if (it % check_every == 0 || it == max_iter) {
-      ST_CUDA(h, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
-      h->d2h_bytes += (int64_t)(c.nsel * sizeof(CocgScal));
-      ST_CUDA(h, cudaStreamSynchronize(s));
-      st_status st = check_launch(h, "cocg");
+      ST_CUDAC(c, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
+      c.d2h += (int64_t)(c.nsel * sizeof(CocgScal));
+      ST_CUDAC(c, cudaStreamSynchronize(s));
+      st_status st = ccheck(c, "cocg");
       if (st != ST_OK) return st;
       int na = 0;
       for (const auto& q : c.scal_h) na += q.active ? 1 : 0;
@@ -892,76 +947,76 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
       if (na == 0) break;
     }
     z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-    PROF(h, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+    PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
          launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-    PROF(h, KC_UPDATE, m * n * 3 * cs, m * n * 8.0,
-         launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+    PROF(h, s, KC_UPDATE, m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
   }
-  ST_CUDA(h, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
-  ST_CUDA(h, cudaStreamSynchronize(s));
+  ST_CUDAC(c, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
+  ST_CUDAC(c, cudaStreamSynchronize(s));
   int worst = 0;
   for (const auto& q : c.scal_h) {
     iters_out = std::max(iters_out, q.iters);
     if (q.status != 0) worst = q.status;
   }
-  if (worst == 4) return fail(h, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
-  if (worst != 0) return fail(h, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
+  if (worst == 4) return cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
+  if (worst != 0) return cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
   return ST_OK;
 }
 
 st_status assemble_rhs(st_handle* h, Component& c) {
   if (c.f_ready) return ST_OK;
-  PROF(h, KC_RHS, (double)(h->nterm_rows + c.nt) * c.nx * 8.0, 2.0 * h->nterm_rows * c.nt * (double)c.nx,
-       launch_rhs_assemble(c.td->rhs_coef, c.sl->loads, c.F, h->nterm_rows, c.nt, c.nx, h->stream));
+  PROF(h, c.cs, KC_RHS, (double)(h->nterm_rows + c.nt) * c.nx * 8.0, 2.0 * h->nterm_rows * c.nt * (double)c.nx,
+       launch_rhs_assemble(c.td->rhs_coef, c.sl->loads, c.F, h->nterm_rows, c.nt, c.nx, c.cs));
   if (c.Fg_all != nullptr)
     for (int i = 0; i < c.nt; ++i)
       launch_load(c.sl->geo, c.sl->sc, c.sl->c2d, c.Fg_all + (size_t)i * c.sl->nall, c.F + (size_t)i * c.nx, 0.0,
-                  1.0, 1, h->stream);
+                  1.0, 1, c.cs);
   c.f_ready = true;
-  return check_launch(h, "rhs");
+  return ccheck(c, "rhs");
 }
 
-st_status read_norm(st_handle* h, const double* v, int64_t n, double& out) {
-  PROF(h, KC_NORM, (double)n * 8.0, 2.0 * n, launch_norm2(v, n, h->part, h->scalar, h->stream));
-  ST_CUDA(h, cudaMemcpyAsync(h->scalar_h, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  h->d2h_bytes += (int64_t)sizeof(double);
-  ST_CUDA(h, cudaStreamSynchronize(h->stream));
-  out = std::sqrt(*h->scalar_h);
-  return check_launch(h, "norm");
+st_status read_norm(st_handle* h, Component& c, const double* v, int64_t n, double& out) {
+  PROF(h, c.cs, KC_NORM, (double)n * 8.0, 2.0 * n, launch_norm2(v, n, c.cpart, c.cscalar, c.cs));
+  int serr = 0;
+  ST_CUDAC(c, cudaMemcpyAsync(&serr, c.cerr, sizeof(int), cudaMemcpyDeviceToHost, c.cs));
+  ST_CUDAC(c, cudaMemcpyAsync(c.cscalar_h, c.cscalar, sizeof(double), cudaMemcpyDeviceToHost, c.cs));
+  c.d2h += (int64_t)(sizeof(double) + sizeof(int));
+  ST_CUDAC(c, cudaStreamSynchronize(c.cs));
+  out = std::sqrt(*c.cscalar_h);
+  if (serr) return cfail(c, ST_ERR_TIMEOUT, "a bounded copy wait in the banded solve timed out");
+  return ccheck(c, "norm");
 }
 
 template <typename R> st_status sweep_time_eig(st_handle* h, Component& c, const double* Rin, int& iters) {
-  st_status s = prepare_work<R>(h, c);
-  if (s != ST_OK) return s;
   Work<R>& w = work_of<R>(c);
   const double cs = sizeof(cx<R>), nx = (double)c.nx;
-  PROF(h, KC_TRANSFORM, c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
-       launch_fwd_transform<R>(c.td->W, Rin, w.G, c.nsel, c.nt, c.nx, h->stream));
-  s = inner_solve<R>(h, c, iters);
+  PROF(h, c.cs, KC_TRANSFORM, c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+       launch_fwd_transform<R>(c.td->W, Rin, w.G, c.nsel, c.nt, c.nx, c.cs));
+  st_status s = inner_solve<R>(h, c, iters);
   if (s != ST_OK) return s;
-  PROF(h, KC_TRANSFORM, 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
-       launch_back_transform<R>(c.td->V, c.td->wq, w.X, c.U, c.nsel, c.nt, c.nx, h->stream));
-  return check_launch(h, "time transforms");
+  PROF(h, c.cs, KC_TRANSFORM, 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+       launch_back_transform<R>(c.td->V, c.td->wq, w.X, c.U, c.nsel, c.nt, c.nx, c.cs));
+  return ccheck(c, "time transforms");
 }
 
 st_status sweep_space_eig(st_handle* h, Component& c, const double* Rin) {
   const double nx = (double)c.nx, nt = c.nt;
-  PROF(h, KC_SPACE_EIG, (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
-       launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, h->stream));
-  PROF(h, KC_SPACE_EIG, (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
-       launch_time_band_solve(c.ab, c.piv, c.KU, c.nt, c.nx, c.kl, c.ku, h->stream));
-  PROF(h, KC_SPACE_EIG, (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
-       launch_gemm_right(c.KU, c.PhiT, c.U, c.nt, c.nx, 1, 1, h->stream));
-  return check_launch(h, "space eigenbasis sweep");
+  PROF(h, c.cs, KC_SPACE_EIG, (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+       launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, c.cs));
+  PROF(h, c.cs, KC_SPACE_EIG, (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
+       launch_time_band_solve(c.ab, c.piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
+  PROF(h, c.cs, KC_SPACE_EIG, (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+       launch_gemm_right(c.KU, c.PhiT, c.U, c.nt, c.nx, 1, 1, c.cs));
+  return ccheck(c, "space eigenbasis sweep");
 }
 
 st_status solve_one(st_handle* h, Component& c) {
   st_status s = assemble_rhs(h, c);
   if (s != ST_OK) return s;
   const size_t n = (size_t)c.nx * c.nt;
-  ST_CUDA(h, cudaMemsetAsync(c.U, 0, n * sizeof(double), h->stream));
+  ST_CUDAC(c, cudaMemsetAsync(c.U, 0, n * sizeof(double), c.cs));
   double fn = 0.0;
-  if ((s = read_norm(h, c.F, (int64_t)n, fn)) != ST_OK) return s;
+  if ((s = read_norm(h, c, c.F, (int64_t)n, fn)) != ST_OK) return s;
   // Refinement stops on the normwise backward error eta = ||R|| / (||S|| ||U|| + ||F||)
   // (the relative residual of an exact solution can be far above rounding
   // when S is ill-conditioned), or when a sweep no longer halves eta.
@@ -990,18 +1045,18 @@ st_status solve_one(st_handle* h, Component& c) {
     }
     c.info.sweeps = sw + 1;
     c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
-    PROF(h, KC_RESIDUAL64, 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
+    PROF(h, c.cs, KC_RESIDUAL64, 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
          (double)n * (4.0 * ipow3(c.sl->geo.d) + 20.0),
          launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, c.U, c.F, c.td->Aband, c.td->Bband, c.KU, c.MU, c.Rv, c.nt,
-                         h->stream));
+                         c.cs));
     double rn = 0.0, un = 0.0;
-    if ((s = read_norm(h, c.Rv, (int64_t)n, rn)) != ST_OK) return s;
-    if ((s = read_norm(h, c.U, (int64_t)n, un)) != ST_OK) return s;
+    if ((s = read_norm(h, c, c.Rv, (int64_t)n, rn)) != ST_OK) return s;
+    if ((s = read_norm(h, c, c.U, (int64_t)n, un)) != ST_OK) return s;
     rel = rn / fn;
     eta = rn / (c.Snorm * un + fn);
     if (!std::isfinite(rel)) {
       c.info.status = ST_ERR_NUMERIC;
-      return fail(h, ST_ERR_NUMERIC, "non-finite residual");
+      return cfail(c, ST_ERR_NUMERIC, "non-finite residual");
     }
     if (eta <= tol || eta > 0.5 * eta_prev) break;
     eta_prev = eta;
@@ -1012,7 +1067,27 @@ st_status solve_one(st_handle* h, Component& c) {
   c.solved = true;
   if (eta > 1e3 * tol && eta > 1e-12) {
     c.info.status = ST_ERR_NOT_CONVERGED;
-    return fail(h, ST_ERR_NOT_CONVERGED, "refinement did not reach the backward-error target");
+    return cfail(c, ST_ERR_NOT_CONVERGED, "refinement did not reach the backward-error target");
+  }
+  return ST_OK;
+}
+
+// Execution context of a component: stream, completion event, reduction
+// scratch, and its workspace prepared for the handle's precision.
+st_status setup_context(st_handle* h, Component& c) {
+  ST_CUDA(h, cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking));
+  ST_CUDA(h, cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+  c.cpart = h->alloc<double>(304);
+  c.cscalar = h->alloc<double>(1);
+  c.cerr = h->alloc<int>(1);
+  ST_NEED(h, c.cpart);
+  ST_NEED(h, c.cscalar);
+  ST_NEED(h, c.cerr);
+  ST_CUDA(h, cudaMemsetAsync(c.cerr, 0, sizeof(int), h->stream));
+  ST_CUDA(h, cudaMallocHost(&c.cscalar_h, sizeof(double)));
+  if (c.method == 0) {
+    st_status s = c.inner64 ? prepare_work<double>(h, c) : prepare_work<float>(h, c);
+    if (s != ST_OK) return s;
   }
   return ST_OK;
 }
@@ -1048,9 +1123,18 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   hp->part = hp->alloc<double>(304);
   hp->scalar = hp->alloc<double>(1);
   hp->dev_err = hp->alloc<int>(1);
-  if (!hp->part || !hp->scalar || !hp->dev_err) {
+  hp->solve_err = hp->alloc<int>(1);
+  if (!hp->part || !hp->scalar || !hp->dev_err || !hp->solve_err) {
     g_create_error = "device allocation failed";
     return ST_ERR_OOM;
+  }
+  if (cudaMemsetAsync(hp->solve_err, 0, sizeof(int), hp->stream) != cudaSuccess) {
+    g_create_error = "cudaMemset failed";
+    return ST_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&hp->entry_ev, cudaEventDisableTiming) != cudaSuccess) {
+    g_create_error = "event creation failed";
+    return ST_ERR_CUDA;
   }
   if (cudaMallocHost(&hp->scalar_h, sizeof(double)) != cudaSuccess) {
     g_create_error = "pinned allocation failed";
@@ -1121,8 +1205,10 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
     c->sl = hp->space[jx].get();
     c->td = &td;
     st_status s = setup_component(hp, *c);
+    if (s == ST_OK) s = setup_context(hp, *c);
     if (s != ST_OK) {
       g_create_error = hp->err;
+      hp->comps.push_back(std::move(c));  // released with the handle
       return s;
     }
     hp->comps.push_back(std::move(c));
@@ -1157,19 +1243,41 @@ st_status st_component(const st_handle* h, int k, st_component_info* info) {
 st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
   if (!h) return ST_ERR_ARG;
   if (k < -1 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
+  const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? (int)h->comps.size() : k + 1;
+  // Component streams start after the work already queued on the handle's stream.
+  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+  std::vector<st_status> st(k1 - k0, ST_OK);
+  for (int i = k0; i < k1; ++i) {
+    Component& c = *h->comps[i];
+    c.err.clear();
+    ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
+  }
+  auto run = [&](int i) { st[i - k0] = solve_one(h, *h->comps[i]); };
+  // Independent components run concurrently, one host thread and one stream
+  // each; with profiling on they run one after the other so that event times
+  // are not shared between overlapping kernels.
+  if (k1 - k0 > 1 && !h->prof_on) {
+    std::vector<std::thread> pool;
+    pool.reserve(k1 - k0);
+    for (int i = k0; i < k1; ++i) pool.emplace_back(run, i);
+    for (auto& t : pool) t.join();
+  } else {
+    for (int i = k0; i < k1; ++i) run(i);
+  }
   st_status worst = ST_OK;
   st_solve_info agg{};
-  const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? (int)h->comps.size() : k + 1;
   for (int i = k0; i < k1; ++i) {
-    st_status s = solve_one(h, *h->comps[i]);
-    const st_solve_info& ci = h->comps[i]->info;
+    Component& c = *h->comps[i];
+    ST_CUDA(h, cudaEventRecord(c.done, c.cs));
+    ST_CUDA(h, cudaStreamWaitEvent(h->stream, c.done, 0));
+    const st_solve_info& ci = c.info;
     agg.sweeps = std::max(agg.sweeps, ci.sweeps);
     agg.max_inner_iters = std::max(agg.max_inner_iters, ci.max_inner_iters);
     agg.rel_residual = std::max(agg.rel_residual, ci.rel_residual);
     agg.backward_error = std::max(agg.backward_error, ci.backward_error);
-    if (s != ST_OK) {
-      worst = s;
-      break;
+    if (st[i - k0] != ST_OK && worst == ST_OK) {
+      worst = st[i - k0];
+      h->err = "component " + std::to_string(i) + ": " + c.err;
     }
   }
   agg.status = worst;
@@ -1248,7 +1356,7 @@ st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
     int64_t nsp = 1;
     for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
     const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
-    PROF(h, KC_COMBINE, outb + inb, (double)nsp * nts * (2.0 * (1 << p.d) + 8.0 * (c1 - c0)),
+    PROF(h, h->stream, KC_COMBINE, outb + inb, (double)nsp * nts * (2.0 * (1 << p.d) + 8.0 * (c1 - c0)),
          launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
   }
   return check_launch(h, "combine");
@@ -1274,7 +1382,11 @@ st_status st_total_dofs(const st_handle* h, int64_t* dofs) {
 st_status st_transfer_bytes(const st_handle* h, int64_t* h2d, int64_t* d2h) {
   if (!h) return ST_ERR_ARG;
   if (h2d) *h2d = h->h2d_bytes;
-  if (d2h) *d2h = h->d2h_bytes;
+  if (d2h) {
+    int64_t s = h->d2h_bytes;
+    for (auto& c : h->comps) s += c->d2h;
+    *d2h = s;
+  }
   return ST_OK;
 }
 

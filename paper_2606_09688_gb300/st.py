@@ -16,10 +16,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libst.so")
 
-ST_OK, ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_OOM, ST_ERR_NOT_CONVERGED, ST_ERR_STATE, ST_ERR_CALLBACK, ST_ERR_NUMERIC = range(8)
+ST_OK, ST_ERR_ARG, ST_ERR_CUDA, ST_ERR_OOM, ST_ERR_NOT_CONVERGED, ST_ERR_STATE, ST_ERR_CALLBACK, ST_ERR_NUMERIC, ST_ERR_TIMEOUT = range(9)
 ST_FP64, ST_FP32_IR = 0, 1
 STATUS_NAMES = {0: "ST_OK", 1: "ST_ERR_ARG", 2: "ST_ERR_CUDA", 3: "ST_ERR_OOM", 4: "ST_ERR_NOT_CONVERGED",
-                5: "ST_ERR_STATE", 6: "ST_ERR_CALLBACK", 7: "ST_ERR_NUMERIC"}
+                5: "ST_ERR_STATE", 6: "ST_ERR_CALLBACK", 7: "ST_ERR_NUMERIC", 8: "ST_ERR_TIMEOUT"}
 
 SPACE_FN = C.CFUNCTYPE(C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
 TIME_FN = C.CFUNCTYPE(C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
