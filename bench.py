@@ -38,6 +38,8 @@ WORKLOADS = {
     # name: (problem factory, target (jx*, jt*), description)
     "layered_2d_n12": (lambda: W.layered_2d(12, 2), (10, 10),
                        "d=2, c^2 in {1,4} (layer at y=0.5), Gaussian x Ricker source, n=12, m=2, 17 components"),
+    "layered_2d_n10": (lambda: W.layered_2d(10, 2), (8, 8),
+                       "d=2, layered c^2, Gaussian x Ricker source, n=10, m=2, 13 components (profiling size)"),
     "standing_wave_1d_n6": (lambda: W.standing_wave(1, 6, 1), (5, 5),
                             "d=1, c=1, u0=sin(pi x), n=6, m=1, 9 components"),
     "random_medium_3d_n10": (lambda: W.random_medium_3d(10, 3), (7, 7),
@@ -178,6 +180,16 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
+def csrc_hash():
+    """Hash of every CUDA/C++ source of the library (a changed kernel invalidates ncu numbers)."""
+    src = os.path.join(ROOT, "paper_2606_09688_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()
+
+
 def traffic_for(kclass):
     """DRAM bytes per launch of a kernel class from the committed ncu summary,
     or None when the kernels have changed since it was taken."""
@@ -186,8 +198,7 @@ def traffic_for(kclass):
         return None
     with open(path) as f:
         d = json.load(f)
-    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2606_09688_gb300", "csrc", "kernels.cu"), "rb").read()).hexdigest()
-    if d.get("kernels_cu_sha256") != h:
+    if d.get("csrc_sha256") != csrc_hash():
         return None
     return d.get("bytes_per_launch", {}).get(kclass)
 
@@ -287,14 +298,25 @@ def run_ours(args):
             barrier()
             ms = maxall(ms)
             stats = None
+            comp_ms = None
             if "profile" not in skip:
                 solver.profile(True)
                 solver.solve(-1, sync=False)
                 solver.combine(target[0], target[1], out)
                 stats = solver.profile_read()
                 solver.profile(False)
+                # each component alone (what bounds the step when they overlap)
+                comp_ms = []
+                for k, ci in enumerate(solver.components()):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    solver.solve(k, sync=False)
+                    b.record(stream)
+                    b.synchronize()
+                    comp_ms.append({"jx": ci.jx, "jt": ci.jt, "method": ci.method, "modes": ci.n_modes,
+                                    "ms": a.elapsed_time(b)})
             results[prec] = dict(ms=ms, value=dofs * world / (ms / 1e3), dofs=dofs, setup_s=setup_s,
-                                 launches=launches, clocks=ck, stats=stats,
+                                 launches=launches, clocks=ck, stats=stats, comp_ms=comp_ms,
                                  sweeps=info.sweeps, inner_iters=info.max_inner_iters,
                                  backward_error=info.backward_error, rel_residual=info.rel_residual,
                                  solver=solver)
@@ -349,6 +371,7 @@ def run_ours(args):
                       "gpu_launches": r["launches"], "sweeps": r["sweeps"], "inner_iters": r["inner_iters"],
                       "backward_error": r["backward_error"], "roofline": roofline(r["stats"], hbm, hbm_src, prec)}
     line["kernels"] = {prec: r["stats"] for prec, r in results.items()}
+    line["components_alone_ms"] = {prec: r["comp_ms"] for prec, r in results.items()}
     print(json.dumps(line), flush=True)
 
 

@@ -180,8 +180,8 @@ const char* st_last_error(const st_handle* h);
  *
  * comps[k]: U = device array of component k's coefficients (n_time x n_space,
  * time-major, the layout of st_component_coeffs), lift = device array of u0 on
- * all (2^jx+1)^d nodes of level jx (NULL if u0 = 0), levels and coefficient.
- * At most 64 components.
+ * all (2^jx+1)^d nodes of level jx (NULL if u0 = 0), levels and the
+ * combination coefficient (+1 or -1).  At most 64 components.
  *
  * Scratch: a fixed 32 MiB array in device global memory, part of the library
  * image, so every GPU that loads the library holds it until the process exits.

@@ -3,17 +3,20 @@
 // method (whole component grids, or the coarsest multigrid level).
 //
 // Storage (per mode q, at q * mstride): row k of F holds column k of L,
-// F[k][t] = L_{k+t,k} (t = 1..bw) and F[k][0] = d_k; row k of G holds row k of L,
+// F[k][t] = L_{k+t,k} (t = 1..bw) and F[k][0] = 1/d_k; row k of G holds row k of L,
 // G[k][t] = L_{k,k-t}.  Rows are padded to an even length ld so that every
 // row starts on a 16-byte boundary (TMA bulk copies).
 //
 // Solve: one warp per mode.  Forward (L y = b, column-oriented with F rows in
 // increasing k) and backward (L^T x = z, column-oriented with G rows in
-// decreasing k) share one routine: a window of the next bw right-hand-side
-// rows lives in registers (row r in slot r mod bw, lane = slot mod 32), the
-// finished row is broadcast with one shuffle, and every lane updates its
-// slots.  Factor rows are streamed into shared memory in chunks by
-// cp.async.bulk with mbarrier completion, two chunks in flight.
+// decreasing k) share one routine.  The window of the bw pending
+// right-hand-side rows is a shift register in registers: at step k, slot j
+// (lane j mod 32, register j / 32) holds row k + j, so every lane applies the
+// same band offsets at every step; row k+1 is broadcast from lane 1 right
+// after its update, the window shifts down by one slot with shuffles, and the
+// row entering at slot bw-1 takes a right-hand-side value staged in shared
+// memory one chunk ahead.  Factor rows are streamed into shared memory in
+// chunks by cp.async.bulk with mbarrier completion, two chunks in flight.
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -115,6 +118,7 @@ __global__ void k_band_ldlt(cx<R>* __restrict__ F, BandLayout L, int* err) {
     }
     __syncthreads();
     for (int t = threadIdx.x + 1; t <= m; t += blockDim.x) Fq[k * ld + t] = col[t] * dinv;
+    if (threadIdx.x == 0) Fq[k * ld] = dinv;  // the solve multiplies by 1/d_k
   }
 }
 
@@ -145,7 +149,8 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
   const size_t stage_elems = (size_t)C * ld;
   cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem);
   cx<R>* stage1 = stage0 + stage_elems;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(stage1 + stage_elems);
+  cx<R>* bin = stage1 + stage_elems;  // 2 x 32 incoming right-hand-side values
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bin + 64);
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -154,12 +159,12 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
   __syncwarp();
   unsigned phase[2] = {0u, 0u};
   const int nchunks = (nrow + C - 1) / C;
+  const int elane = (bw - 1) & 31, eslot = (bw - 1) >> 5;  // slot bw-1: where rows enter
   cx<R>* dst = x + (int64_t)q * vstride;
+  const cx<R> zero = mk<R>(0, 0);
   for (int pass = 0; pass < 2; ++pass) {
     const cx<R>* Mq = (pass == 0 ? F : G) + (int64_t)q * L.mstride;
     const cx<R>* src = pass == 0 ? b + (int64_t)q * vstride : dst;
-    // chunk c holds the pass-order rows c*C .. c*C+cnt-1; in memory they are
-    // rows klo .. klo+cnt-1 (increasing), i.e. reversed for the backward pass
     auto chunk = [&](int c, int& klo, int& cnt) {
       const int k0 = c * C;
       cnt = min(C, nrow - k0);
@@ -173,26 +178,30 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
       mbar_expect_tx(&bar[c & 1], bytes);
       bulk_g2s(st, Mq + (int64_t)klo * ld, bytes, &bar[c & 1]);
     };
+    auto at = [&](int rp) -> cx<R> {  // right-hand side of pass-order row rp (zero past the end)
+      if (rp >= nrow) return zero;
+      return src[pass == 0 ? rp : nrow - 1 - rp];
+    };
     if (lane == 0) {
       issue(0);
       if (nchunks > 1) issue(1);
     }
-    auto at = [&](int rp) -> cx<R> {  // right-hand side of pass-order row rp
-      const int r = pass == 0 ? rp : nrow - 1 - rp;
-      return src[r];
-    };
-    cx<R> v[SLOTS], nb[SLOTS];
-    int tc[SLOTS];
+    // rows entering during chunk c: pass-order rows c*C + i + bw, i < C (one per lane)
+    bin[lane] = lane < C ? at(lane + bw) : zero;
+    cx<R> v[SLOTS];
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
       const int j = lane + 32 * s;
-      v[s] = (j < bw && j < nrow) ? at(j) : mk<R>(0, 0);
-      nb[s] = (j < bw && j + bw < nrow) ? at(j + bw) : mk<R>(0, 0);
-      tc[s] = j;
+      v[s] = j < bw ? at(j) : zero;
     }
-    int jk = 0;  // slot of the row finished at this step (pass-order row mod bw)
+    __syncwarp();
+    cx<R> y;  // value of the row finished at the current step
+    y.re = __shfl_sync(0xffffffffu, v[0].re, 0);
+    y.im = __shfl_sync(0xffffffffu, v[0].im, 0);
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
+    for (int c = 0; c < nchunks; ++c) {
+      // prefetch the right-hand sides entering during the next chunk
+      const cx<R> pre = lane < C ? at((c + 1) * C + lane + bw) : zero;
       ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
@@ -202,45 +211,239 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
       int klo, cnt;
       chunk(c, klo, cnt);
       const cx<R>* st = (c & 1) ? stage1 : stage0;
+      const cx<R>* bc = bin + (c & 1) * 32;
       for (int i = 0; i < cnt; ++i) {
         const int kp = c * C + i;
         const int k = pass == 0 ? kp : nrow - 1 - kp;
         const cx<R>* row = st + (size_t)(k - klo) * ld;
-        cx<R> mine = v[0];
-#pragma unroll
-        for (int s = 1; s < SLOTS; ++s)
-          if (tc[s] == 0) mine = v[s];
-        const int owner = jk & 31;
-        cx<R> y;
-        y.re = __shfl_sync(0xffffffffu, mine.re, owner);
-        y.im = __shfl_sync(0xffffffffu, mine.im, owner);
-        if (lane == owner) dst[k] = pass == 0 ? cdiv(y, row[0]) : y;
+        if (lane == 0) {
+          const cx<R> dinv = row[0];
+          dst[k] = pass == 0 ? y * dinv : y;
+        }
+        // update the rows k+j (slots j >= 1) and the entering row k+bw
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
           const int j = lane + 32 * s;
-          if (j >= bw) continue;
-          int t = tc[s];
-          if (t == 0) {  // this slot takes pass-order row kp + bw
-            t = bw;
-            v[s] = nb[s];
-            const int rn = kp + 2 * bw;
-            nb[s] = rn < nrow ? at(rn) : mk<R>(0, 0);
-            tc[s] = bw - 1;
-          } else {
-            tc[s] = t - 1;
-          }
-          if (kp + t < nrow) {
-            const cx<R> a = row[t];
+          if (j >= 1 && j < bw) {
+            const cx<R> a = row[j];
             v[s] = mk<R>(v[s].re - (a.re * y.re - a.im * y.im), v[s].im - (a.re * y.im + a.im * y.re));
           }
         }
-        jk = (jk + 1 == bw) ? 0 : jk + 1;
+        cx<R> ent = zero;
+        if (lane == elane) {
+          const cx<R> a = row[bw];
+          const cx<R> bi = bc[i];
+          ent = mk<R>(bi.re - (a.re * y.re - a.im * y.im), bi.im - (a.re * y.im + a.im * y.re));
+        }
+        // row k+1 (slot 1, lane 1) is final: broadcast it, then shift the window
+        // (with bw = 1 the next row is the entering one)
+        const cx<R> src_next = bw > 1 ? v[0] : ent;
+        cx<R> yn;
+        yn.re = __shfl_sync(0xffffffffu, src_next.re, bw > 1 ? 1 : elane);
+        yn.im = __shfl_sync(0xffffffffu, src_next.im, bw > 1 ? 1 : elane);
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+          cx<R> up;
+          up.re = __shfl_down_sync(0xffffffffu, v[s].re, 1);
+          up.im = __shfl_down_sync(0xffffffffu, v[s].im, 1);
+          if (s + 1 < SLOTS) {
+            cx<R> nx;
+            nx.re = __shfl_sync(0xffffffffu, v[s + 1].re, 0);
+            nx.im = __shfl_sync(0xffffffffu, v[s + 1].im, 0);
+            if (lane == 31) up = nx;
+          }
+          v[s] = up;
+        }
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s)
+          if (s == eslot && lane == elane) v[s] = ent;
+        y = yn;
       }
+      __syncwarp();
+      bin[((c + 1) & 1) * 32 + lane] = pre;
       __syncwarp();
       if (lane == 0 && c + 2 < nchunks) issue(c + 2);
     }
     if (!ok) {
       // give the copies still in flight a bounded chance to land, then report
+      if (lane == 0) {
+        atomicExch(err, 2);
+        for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
+      }
+      return;
+    }
+    __syncwarp();
+  }
+}
+
+// Variant for bw = 32 * SLOTS (every 2D grid: bw = 2^j): rows keep their
+// register slot for their whole life (row r in lane r mod 32, register
+// (r mod bw) / 32), so no data moves between lanes except the broadcast of
+// the finished row.  Chunks are 32 rows, one group of 32 unrolled steps in
+// which every band offset is a compile-time constant; SG = chunk mod SLOTS is
+// the register that holds the rows finished during the chunk.
+template <typename R, int SLOTS, int PASS, int SG>
+__device__ __forceinline__ void band_group32(const cx<R>* __restrict__ st, int c, int nrow, int ld, int lane,
+                                             cx<R> (&v)[SLOTS], const cx<R>& bcur, cx<R>& y,
+                                             cx<R>* __restrict__ dst) {
+  constexpr int bw = 32 * SLOTS;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const cx<R>* row = st + (size_t)(PASS == 0 ? i : 31 - i) * ld;
+    if (lane == i) {
+      const int kp = 32 * c + i;
+      const int k = PASS == 0 ? kp : nrow - 1 - kp;
+      dst[k] = PASS == 0 ? y * row[0] : y;
+    }
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+      if (s == SG) {
+        // lanes after i hold rows kp + (lane - i); lanes before i already hold
+        // rows entered during this chunk (t = lane - i + bw); lane i takes row kp + bw
+        const int t = lane - i + (lane <= i ? bw : 0);
+        const cx<R> a = row[t];
+        const cx<R> base = lane == i ? bcur : v[s];
+        v[s] = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, base.re)), fma(-a.re, y.im, fma(-a.im, y.re, base.im)));
+      } else {
+        const int d = (s - SG + SLOTS) % SLOTS;
+        const cx<R> a = row[lane - i + 32 * d];
+        v[s] = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, v[s].re)), fma(-a.re, y.im, fma(-a.im, y.re, v[s].im)));
+      }
+    }
+    const int nslot = (i < 31) ? SG : (SG + 1) % SLOTS;
+    y.re = __shfl_sync(0xffffffffu, v[nslot].re, (i + 1) & 31);
+    y.im = __shfl_sync(0xffffffffu, v[nslot].im, (i + 1) & 31);
+  }
+}
+
+// One step with a run-time step index (the last, partial chunk).
+template <typename R, int SLOTS, int PASS>
+__device__ __forceinline__ void band_step_rt(const cx<R>* __restrict__ row, int i, int sg, int c, int nrow,
+                                             int lane, cx<R> (&v)[SLOTS], const cx<R>& bcur, cx<R>& y,
+                                             cx<R>* __restrict__ dst) {
+  constexpr int bw = 32 * SLOTS;
+  if (lane == i) {
+    const int kp = 32 * c + i;
+    const int k = PASS == 0 ? kp : nrow - 1 - kp;
+    dst[k] = PASS == 0 ? y * row[0] : y;
+  }
+#pragma unroll
+  for (int s = 0; s < SLOTS; ++s) {
+    int t;
+    cx<R> base = v[s];
+    if (s == sg) {
+      t = lane - i + (lane <= i ? bw : 0);
+      if (lane == i) base = bcur;
+    } else {
+      t = lane - i + 32 * ((s - sg + SLOTS) % SLOTS);
+    }
+    const cx<R> a = row[t];
+    v[s] = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, base.re)), fma(-a.re, y.im, fma(-a.im, y.re, base.im)));
+  }
+  const int nslot = (i < 31) ? sg : (sg + 1) % SLOTS;
+  cx<R> src = v[0];
+#pragma unroll
+  for (int s = 1; s < SLOTS; ++s)
+    if (s == nslot) src = v[s];
+  y.re = __shfl_sync(0xffffffffu, src.re, (i + 1) & 31);
+  y.im = __shfl_sync(0xffffffffu, src.im, (i + 1) & 31);
+}
+
+template <typename R, int SLOTS, int PASS>
+__device__ __forceinline__ void band_group_dispatch(const cx<R>* st, int c, int nrow, int ld, int lane,
+                                                    cx<R> (&v)[SLOTS], const cx<R>& bcur, cx<R>& y, cx<R>* dst) {
+  const int sg = c % SLOTS;
+  if (SLOTS == 1 || sg == 0) band_group32<R, SLOTS, PASS, 0>(st, c, nrow, ld, lane, v, bcur, y, dst);
+  else if (SLOTS >= 2 && sg == 1) band_group32<R, SLOTS, PASS, (SLOTS >= 2 ? 1 : 0)>(st, c, nrow, ld, lane, v, bcur, y, dst);
+  else if (SLOTS >= 4 && sg == 2) band_group32<R, SLOTS, PASS, (SLOTS >= 4 ? 2 : 0)>(st, c, nrow, ld, lane, v, bcur, y, dst);
+  else if (SLOTS >= 4 && sg == 3) band_group32<R, SLOTS, PASS, (SLOTS >= 4 ? 3 : 0)>(st, c, nrow, ld, lane, v, bcur, y, dst);
+}
+
+template <typename R, int SLOTS>
+__global__ void __launch_bounds__(32) k_band_solve_p2(const cx<R>* __restrict__ F, const cx<R>* __restrict__ G,
+                                                      BandLayout L, const cx<R>* __restrict__ b,
+                                                      cx<R>* __restrict__ x, const CocgScal* __restrict__ scal,
+                                                      int64_t vstride, int* err) {
+  constexpr int C = 32, bw = 32 * SLOTS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = blockIdx.x;
+  if (scal != nullptr && !scal[q].active) return;
+  const int lane = threadIdx.x;
+  const int ld = L.ld, nrow = (int)L.nrow;
+  const size_t stage_elems = (size_t)C * ld;
+  cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem);
+  cx<R>* stage1 = stage0 + stage_elems;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage1 + stage_elems);
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  unsigned phase[2] = {0u, 0u};
+  const int nchunks = (nrow + C - 1) / C;
+  cx<R>* dst = x + (int64_t)q * vstride;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    const cx<R>* Mq = (pass == 0 ? F : G) + (int64_t)q * L.mstride;
+    const cx<R>* src = pass == 0 ? b + (int64_t)q * vstride : dst;
+    auto chunk = [&](int c, int& klo, int& cnt) {
+      const int k0 = c * C;
+      cnt = min(C, nrow - k0);
+      klo = pass == 0 ? k0 : nrow - k0 - cnt;
+    };
+    auto issue = [&](int c) {
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      cx<R>* st = (c & 1) ? stage1 : stage0;
+      const unsigned bytes = (unsigned)((size_t)cnt * ld * sizeof(cx<R>));
+      mbar_expect_tx(&bar[c & 1], bytes);
+      bulk_g2s(st, Mq + (int64_t)klo * ld, bytes, &bar[c & 1]);
+    };
+    auto at = [&](int rp) -> cx<R> {
+      if (rp >= nrow) return zero;
+      return src[pass == 0 ? rp : nrow - 1 - rp];
+    };
+    if (lane == 0) {
+      issue(0);
+      if (nchunks > 1) issue(1);
+    }
+    cx<R> v[SLOTS];
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) v[s] = at(lane + 32 * s);
+    cx<R> bcur = at(lane + bw), bnext = at(C + lane + bw);
+    cx<R> y;
+    y.re = __shfl_sync(0xffffffffu, v[0].re, 0);
+    y.im = __shfl_sync(0xffffffffu, v[0].im, 0);
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      phase[c & 1] ^= 1u;
+      const cx<R> bnn = at((c + 2) * C + lane + bw);  // entering rows of chunk c + 2
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      const cx<R>* st = (c & 1) ? stage1 : stage0;
+      if (cnt == C) {
+        if (pass == 0) band_group_dispatch<R, SLOTS, 0>(st, c, nrow, ld, lane, v, bcur, y, dst);
+        else band_group_dispatch<R, SLOTS, 1>(st, c, nrow, ld, lane, v, bcur, y, dst);
+      } else {
+        const int sg = c % SLOTS;
+        for (int i = 0; i < cnt; ++i) {
+          const cx<R>* row = st + (size_t)(pass == 0 ? i : cnt - 1 - i) * ld;
+          if (pass == 0) band_step_rt<R, SLOTS, 0>(row, i, sg, c, nrow, lane, v, bcur, y, dst);
+          else band_step_rt<R, SLOTS, 1>(row, i, sg, c, nrow, lane, v, bcur, y, dst);
+        }
+      }
+      bcur = bnext;
+      bnext = bnn;
+      __syncwarp();
+      if (lane == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    if (!ok) {
       if (lane == 0) {
         atomicExch(err, 2);
         for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
@@ -258,6 +461,15 @@ template <typename R, int SLOTS> void set_smem_attr(size_t bytes) {
   std::lock_guard<std::mutex> lock(g_attr_mu);
   if (bytes > done) {
     cudaFuncSetAttribute(k_band_solve_w<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
+template <typename R, int SLOTS> void set_smem_attr_p2(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_solve_p2<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done = bytes;
   }
 }
@@ -289,15 +501,31 @@ void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int
 
 int band_chunk_rows(const BandLayout& L, size_t elem) {
   int C = (int)(32768 / (L.ld * elem));
-  C = C < 2 ? 2 : (C > 64 ? 64 : C);
+  C = C < 2 ? 2 : (C > 32 ? 32 : C);  // at most one incoming row per lane and chunk
   return C & ~1;
 }
 
 template <typename R>
 bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, const cx<R>* b, cx<R>* x,
                        const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s) {
+  // power-of-two bandwidths (the 2D grids): fixed-slot kernel with 32-row chunks
+  const size_t smem32 = 2 * (size_t)32 * L.ld * sizeof(cx<R>) + 2 * sizeof(uint64_t);
+  if (smem32 <= 160 * 1024 && (L.bw == 32 || L.bw == 64 || L.bw == 128)) {
+    if (L.bw == 32) {
+      set_smem_attr_p2<R, 1>(smem32);
+      k_band_solve_p2<R, 1><<<nmodes, 32, smem32, s>>>(F, G, L, b, x, scal, vstride, err);
+    } else if (L.bw == 64) {
+      set_smem_attr_p2<R, 2>(smem32);
+      k_band_solve_p2<R, 2><<<nmodes, 32, smem32, s>>>(F, G, L, b, x, scal, vstride, err);
+    } else {
+      set_smem_attr_p2<R, 4>(smem32);
+      k_band_solve_p2<R, 4><<<nmodes, 32, smem32, s>>>(F, G, L, b, x, scal, vstride, err);
+    }
+    note_launches(1);
+    return true;
+  }
   const int C = band_chunk_rows(L, sizeof(cx<R>));
-  const size_t smem = 2 * (size_t)C * L.ld * sizeof(cx<R>) + 2 * sizeof(uint64_t);
+  const size_t smem = (2 * (size_t)C * L.ld + 64) * sizeof(cx<R>) + 2 * sizeof(uint64_t);
   if (L.bw <= 32) {
     set_smem_attr<R, 1>(smem);
     k_band_solve_w<R, 1><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);

@@ -618,34 +618,30 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
   double v = 0.0;
   if (Yprev != nullptr) {
     // bilinear prolongation from level j-1 (all nodes): per direction the
-    // coarse node P/2 (even P) or (P-1)/2 and (P+1)/2 with weight 1/2
+    // coarse node P/2 (even P) or the pair (P-1)/2, (P+1)/2; the valid corners
+    // are summed and scaled once by 2^-(number of odd directions)
     const int Nc = Nj >> 1;
-    const double* Ys = Yprev;
     int64_t ncs = 1;
 #pragma unroll
     for (int k = 0; k < D; ++k) ncs *= (Nc + 1);
-    Ys += (int64_t)s * ncs;
+    const double* Ys = Yprev + (int64_t)s * ncs;
+    int odd = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) odd += P[k] & 1;
 #pragma unroll
     for (int e = 0; e < (1 << D); ++e) {
       bool ok = true;
-      double w = 1.0;
       int64_t idx = 0, st = 1;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const int bit = (e >> k) & 1;
-        int G;
-        if ((P[k] & 1) == 0) {
-          ok = ok && (bit == 0);
-          G = P[k] >> 1;
-        } else {
-          G = (P[k] >> 1) + bit;
-          w *= 0.5;
-        }
-        idx += (int64_t)G * st;
+        ok = ok && (bit == 0 || (P[k] & 1));
+        idx += (int64_t)((P[k] >> 1) + bit) * st;
         st *= (Nc + 1);
       }
-      if (ok) v = fma(w, Ys[idx], v);
+      if (ok) v += Ys[idx];
     }
+    if (odd) v *= (odd == 1 ? 0.5 : (odd == 2 ? 0.25 : 0.125));
   }
   bool interior = true;
 #pragma unroll
@@ -680,7 +676,7 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
       }
       val += cc.lift[ia];
     }
-    v = fma((double)cc.coef, val, v);
+    v = cc.coef > 0 ? v + val : v - val;
   }
   Y[(int64_t)s * nsp + p] = v;
 }

@@ -84,7 +84,8 @@ extern "C" st_status st_combine_noalloc(const st_comb_input* comps, int ncomp, i
   // components ordered by their combination level min(jx, jx*)
   std::vector<int> order(ncomp);
   for (int c = 0; c < ncomp; ++c) {
-    if (comps[c].U == nullptr || comps[c].jx < 1 || comps[c].jx > 14 || comps[c].jt < 0 || comps[c].jt > 14)
+    if (comps[c].U == nullptr || comps[c].jx < 1 || comps[c].jx > 14 || comps[c].jt < 0 || comps[c].jt > 14 ||
+        (comps[c].coef != 1 && comps[c].coef != -1))
       return ST_ERR_ARG;
     order[c] = c;
   }
