@@ -38,6 +38,8 @@ WORKLOADS = {
     # name: (problem factory, target (jx*, jt*), description)
     "layered_2d_n12": (lambda: W.layered_2d(12, 2), (10, 10),
                        "d=2, c^2 in {1,4} (layer at y=0.5), Gaussian x Ricker source, n=12, m=2, 17 components"),
+    "layered_2d_n12_t6": (lambda: W.layered_2d(12, 2), (6, 6),
+                          "the layered 2D workload with a (6,6) target grid (profiling the solves)"),
     "layered_2d_n10": (lambda: W.layered_2d(10, 2), (8, 8),
                        "d=2, layered c^2, Gaussian x Ricker source, n=10, m=2, 13 components (profiling size)"),
     "standing_wave_1d_n6": (lambda: W.standing_wave(1, 6, 1), (5, 5),
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"],
                     help="precision of the headline value; the other one is reported beside it")
     ap.add_argument("--skip", default="", help="comma list of: other,profile,e2e,cpu")
+    ap.add_argument("--only-component", type=int, default=-1,
+                    help="profiling aid: each step solves only this component (no combination)")
     return ap.parse_args()
 
 
@@ -203,11 +207,14 @@ def traffic_for(kclass):
     return d.get("bytes_per_launch", {}).get(kclass)
 
 
-def timed_steps(solver, out, target, steps, stream, torch):
+def timed_steps(solver, out, target, steps, stream, torch, only=-1):
     jx, jt = target
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for _ in range(steps):
+        if only >= 0:
+            solver.solve(only, sync=False)
+            continue
         solver.solve(-1, sync=False)
         solver.combine(jx, jt, out)
     end.record(stream)
@@ -282,16 +289,18 @@ def run_ours(args):
             setup_s = time.perf_counter() - t0
             dofs = solver.total_dofs
             for _ in range(args.warmup):
-                solver.solve(-1, sync=False)
+                solver.solve(args.only_component, sync=False)
+                if args.only_component < 0:
+                    solver.combine(target[0], target[1], out)
+            info = solver.solve(args.only_component, sync=True)
+            if args.only_component < 0:
                 solver.combine(target[0], target[1], out)
-            info = solver.solve(-1, sync=True)
-            solver.combine(target[0], target[1], out)
             barrier()
             l0 = solver.kernel_launches
             clocks = Clocks()
             if prec == args.precision:
                 clocks.start()
-            ms = timed_steps(solver, out, target, args.steps, stream, torch)
+            ms = timed_steps(solver, out, target, args.steps, stream, torch, args.only_component)
             launches = (solver.kernel_launches - l0) // args.steps
             ck = clocks.stop(getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", None)) \
                 if prec == args.precision else None

@@ -64,10 +64,19 @@ struct Geo {
 // node and its neighbour is (sum of c^2 over the cells that hold both) x ke,
 // since the element matrix entry only depends on delta; the mass entry is
 // the assembled constant mtot (cell count included).
-struct StencilCoef {
-  double ke[27];
-  double mtot[27];
+template <typename R> struct StencilCoefT {
+  R ke[27];
+  R mtot[27];
 };
+using StencilCoef = StencilCoefT<double>;
+inline StencilCoefT<float> to_float(const StencilCoef& s) {
+  StencilCoefT<float> f;
+  for (int i = 0; i < 27; ++i) {
+    f.ke[i] = (float)s.ke[i];
+    f.mtot[i] = (float)s.mtot[i];
+  }
+  return f;
+}
 
 __host__ __device__ constexpr int ipow3(int d) { return d == 0 ? 1 : 3 * ipow3(d - 1); }
 

@@ -89,7 +89,7 @@ template <int D> __device__ __forceinline__ bool neighbour(const int i[3], int s
 
 // ------------------------------------------------------------------ stencils
 template <int D, typename R, int OP>
-__global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const R* __restrict__ c2,
+__global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
                                                     const cx<R>* __restrict__ x, const cx<R>* __restrict__ b,
                                                     cx<R>* __restrict__ y, const cx<R>* __restrict__ lam,
                                                     const CocgScal* __restrict__ scal, int64_t stride, R omega) {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const
   R S[NS];
   cell_sums<D, R>(c2, g.N, i, S);
   const cx<R> l = lam[q];
-  const cx<R> diag = fma_s(R(sc.mtot[CEN]), l, mk<R>(S[CEN] * R(sc.ke[CEN]), R(0)));
+  const cx<R> diag = fma_s(sc.mtot[CEN], l, mk<R>(S[CEN] * sc.ke[CEN], R(0)));
   const int64_t base = (int64_t)q * stride;
   if (OP == OP_JACOBI_ZERO) {
     y[base + a] = omega * cdiv(b[base + a], diag);
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const
     int64_t off;
     if (neighbour<D>(i, s, g.n, off)) {
       const cx<R> v = x[base + a + off];
-      ak = fma_s(S[s] * R(sc.ke[s]), v, ak);
-      am = fma_s(R(sc.mtot[s]), v, am);
+      ak = fma_s(S[s] * sc.ke[s], v, ak);
+      am = fma_s(sc.mtot[s], v, am);
     }
   }
   const cx<R> Ax = fma_c(l, am, ak);
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoef sc, const
 }
 
 template <int D, typename R>
-void stencil_dispatch(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                       cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
                       cudaStream_t s) {
   dim3 grid(blocks_for(g.nnodes), nmodes);
@@ -219,6 +219,21 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(Geo gf, Geo gc, const cx
 
 // ------------------------------------------------------------ COCG pieces
 enum { RED_BB = 0, RED_ALPHA = 1, RED_RR = 2, RED_BETA = 3, RED_RHO0 = 4 };
+
+template <typename R> __device__ __forceinline__ cx<R> step_alpha(const CocgScal& S);
+template <> __device__ __forceinline__ cx<double> step_alpha<double>(const CocgScal& S) {
+  return mk<double>(S.alpha_re, S.alpha_im);
+}
+template <> __device__ __forceinline__ cx<float> step_alpha<float>(const CocgScal& S) {
+  return mk<float>(S.alpha_f[0], S.alpha_f[1]);
+}
+template <typename R> __device__ __forceinline__ cx<R> step_beta(const CocgScal& S);
+template <> __device__ __forceinline__ cx<double> step_beta<double>(const CocgScal& S) {
+  return mk<double>(S.beta_re, S.beta_im);
+}
+template <> __device__ __forceinline__ cx<float> step_beta<float>(const CocgScal& S) {
+  return mk<float>(S.beta_f[0], S.beta_f[1]);
+}
 
 template <typename R> __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -310,6 +325,8 @@ __global__ void k_reduce_final(CocgScal* __restrict__ scal, const double* __rest
     // alpha = rho / (p . w)
     S.alpha_re = (S.rho_re * v.re + S.rho_im * v.im) / den;
     S.alpha_im = (S.rho_im * v.re - S.rho_re * v.im) / den;
+    S.alpha_f[0] = (float)S.alpha_re;
+    S.alpha_f[1] = (float)S.alpha_im;
   } else if (WHICH == RED_RR) {
     S.rr = v.re;
     S.iters += 1;
@@ -331,6 +348,8 @@ __global__ void k_reduce_final(CocgScal* __restrict__ scal, const double* __rest
     }
     S.beta_re = (v.re * S.rho_re + v.im * S.rho_im) / den;
     S.beta_im = (v.im * S.rho_re - v.re * S.rho_im) / den;
+    S.beta_f[0] = (float)S.beta_re;
+    S.beta_f[1] = (float)S.beta_im;
     S.rho_re = v.re;
     S.rho_im = v.im;
   }
@@ -354,7 +373,7 @@ __global__ void __launch_bounds__(kBlock) k_update_xr(cx<R>* __restrict__ x, cx<
                                                       int64_t n, int64_t stride) {
   const int q = blockIdx.y;
   if (!scal[q].active) return;
-  const cx<R> al = mk<R>((R)scal[q].alpha_re, (R)scal[q].alpha_im);
+  const cx<R> al = step_alpha<R>(scal[q]);
   const cx<R> nal = mk<R>(-al.re, -al.im);
   cx<R> acc = mk<R>(0, 0);
   const int64_t base = (int64_t)q * stride;
@@ -383,7 +402,7 @@ __global__ void __launch_bounds__(kBlock) k_update_p(cx<R>* __restrict__ p, cons
   if (first) {
     p[e] = z[e];
   } else {
-    const cx<R> be = mk<R>((R)scal[q].beta_re, (R)scal[q].beta_im);
+    const cx<R> be = step_beta<R>(scal[q]);
     p[e] = fma_c(be, p[e], z[e]);
   }
 }
@@ -593,99 +612,129 @@ __global__ void k_time_band_solve(const double* __restrict__ ab, const int* __re
 // Level by level, Y_j = P Y_{j-1} + sum_{components at level j} c_k u_k(., t_s),
 // on all nodes of level j (boundary included, for the lift by u0); a component
 // finer than the target level is injected (its nodes contain the target nodes).
+template <int D> __device__ __forceinline__ double comp_value(const CombComp& cc, int j, const int P[3], int s,
+                                                              int nts, int c, const double* __restrict__ tbv,
+                                                              const int* __restrict__ tspan, bool interior) {
+  const int sh = cc.jx - j;  // >= 0: injection from a finer component grid
+  const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
+  double val = 0.0;
+  if (interior) {
+    int64_t ii = 0, si = 1, nx = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ii += (int64_t)((P[k] << sh) - 1) * si;
+      si *= n;
+      nx *= n;
+    }
+    const int span = tspan[(int64_t)c * nts + s];
+    const double* tb = tbv + ((int64_t)c * nts + s) * 3;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int row = span + t - 1;
+      if (row >= 0 && row < nt) val = fma(tb[t], cc.U[(int64_t)row * nx + ii], val);
+    }
+  }
+  if (cc.lift != nullptr) {
+    int64_t ia = 0, sa = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ia += (int64_t)(P[k] << sh) * sa;
+      sa *= (N + 1);
+    }
+    val += cc.lift[ia];
+  }
+  return val;
+}
+
+// One thread per node Q of level j-1 (all nodes, boundary included): it
+// produces the level-j nodes P = 2Q + e, e in {0,1}^d (those inside the grid).
+// Their prolongated values are formed separably, direction by direction
+// (value at the odd node = half the sum of its two coarse neighbours), so
+// each fine node costs about two FP64 operations; the components of this
+// level are then added node by node.  Without Yprev (the coarsest level of
+// the combination) only the components are evaluated.
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __restrict__ Yprev,
                                                        const CombComp* __restrict__ comps, int c0, int c1,
                                                        const double* __restrict__ tbv, const int* __restrict__ tspan,
-                                                       int nts, double* __restrict__ Y, FastDiv dN1) {
+                                                       int nts, double* __restrict__ Y, FastDiv dQ1) {
   const int s = blockIdx.y;
-  const int Nj = 1 << j;
-  int64_t nsp = 1;
+  const int Nj = 1 << j, Nc = Nj >> 1;
+  int64_t ncs = 1, nsp = 1;
 #pragma unroll
-  for (int k = 0; k < D; ++k) nsp *= (Nj + 1);
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nsp) return;
-  int P[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    ncs *= (Nc + 1);
+    nsp *= (Nj + 1);
+  }
+  const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (qi >= ncs) return;
+  int Q[3] = {0, 0, 0};
   {
-    unsigned r = (unsigned)p;
+    unsigned r = (unsigned)qi;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const unsigned qq = fdiv(r, dN1);
-      P[k] = (int)(r - qq * (unsigned)(Nj + 1));
+      const unsigned qq = fdiv(r, dQ1);
+      Q[k] = (int)(r - qq * (unsigned)(Nc + 1));
       r = qq;
     }
   }
-  double v = 0.0;
+  constexpr int NE = 1 << D;
+  double f[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) f[e] = 0.0;
   if (Yprev != nullptr) {
-    // bilinear prolongation from level j-1 (all nodes): per direction the
-    // coarse node P/2 (even P) or the pair (P-1)/2, (P+1)/2; the valid corners
-    // are summed and scaled once by 2^-(number of odd directions)
-    const int Nc = Nj >> 1;
-    int64_t ncs = 1;
-#pragma unroll
-    for (int k = 0; k < D; ++k) ncs *= (Nc + 1);
     const double* Ys = Yprev + (int64_t)s * ncs;
-    int odd = 0;
+    // coarse corners Q + e (zero outside the grid: those only feed fine nodes outside it)
 #pragma unroll
-    for (int k = 0; k < D; ++k) odd += P[k] & 1;
-#pragma unroll
-    for (int e = 0; e < (1 << D); ++e) {
+    for (int e = 0; e < NE; ++e) {
       bool ok = true;
       int64_t idx = 0, st = 1;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const int bit = (e >> k) & 1;
-        ok = ok && (bit == 0 || (P[k] & 1));
-        idx += (int64_t)((P[k] >> 1) + bit) * st;
+        const int b = (e >> k) & 1;
+        ok = ok && (Q[k] + b <= Nc);
+        idx += (int64_t)(Q[k] + b) * st;
         st *= (Nc + 1);
       }
-      if (ok) v += Ys[idx];
+      f[e] = ok ? Ys[idx] : 0.0;
     }
-    if (odd) v *= (odd == 1 ? 0.5 : (odd == 2 ? 0.25 : 0.125));
+    // separable prolongation: along direction k, bit k = 1 becomes the midpoint
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+      for (int e = 0; e < NE; ++e)
+        if ((e >> k) & 1) f[e] = 0.5 * (f[e ^ (1 << k)] + f[e]);
+    }
   }
-  bool interior = true;
 #pragma unroll
-  for (int k = 0; k < D; ++k) interior = interior && P[k] >= 1 && P[k] <= Nj - 1;
-  for (int c = c0; c < c1; ++c) {
-    const CombComp cc = comps[c];
-    const int sh = cc.jx - j;  // >= 0: injection from a finer component grid
-    const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
-    double val = 0.0;
-    if (interior) {
-      int64_t ii = 0, si = 1, nx = 1;
+  for (int e = 0; e < NE; ++e) {
+    int P[3] = {0, 0, 0};
+    bool inside = true, interior = true;
+    int64_t pidx = 0, st = 1;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        ii += (int64_t)((P[k] << sh) - 1) * si;
-        si *= n;
-        nx *= n;
-      }
-      const int span = tspan[(int64_t)c * nts + s];
-      const double* tb = tbv + ((int64_t)c * nts + s) * 3;
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int row = span + t - 1;
-        if (row >= 0 && row < nt) val = fma(tb[t], cc.U[(int64_t)row * nx + ii], val);
-      }
+    for (int k = 0; k < D; ++k) {
+      P[k] = 2 * Q[k] + ((e >> k) & 1);
+      inside = inside && P[k] <= Nj;
+      interior = interior && P[k] >= 1 && P[k] <= Nj - 1;
+      pidx += (int64_t)P[k] * st;
+      st *= (Nj + 1);
     }
-    if (cc.lift != nullptr) {
-      int64_t ia = 0, sa = 1;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        ia += (int64_t)(P[k] << sh) * sa;
-        sa *= (N + 1);
-      }
-      val += cc.lift[ia];
+    if (!inside) continue;
+    double v = f[e];
+    for (int c = c0; c < c1; ++c) {
+      const CombComp cc = comps[c];
+      const double val = comp_value<D>(cc, j, P, s, nts, c, tbv, tspan, interior);
+      v = cc.coef > 0 ? v + val : v - val;
     }
-    v = cc.coef > 0 ? v + val : v - val;
+    Y[(int64_t)s * nsp + pidx] = v;
   }
-  Y[(int64_t)s * nsp + p] = v;
 }
 
 }  // namespace
 
 // ================================================================ wrappers
 template <typename R>
-void launch_stencil(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+void launch_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                     cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
                     cudaStream_t s) {
   count(1);
@@ -816,10 +865,10 @@ void launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt,
 void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,
                        const int* tspan, int nts, double* Y, cudaStream_t s) {
   count(1);
-  int64_t nsp = 1;
-  for (int k = 0; k < d; ++k) nsp *= ((1 << j) + 1);
-  dim3 grid(blocks_for(nsp), nts);
-  const FastDiv f = make_fastdiv((unsigned)((1 << j) + 1));
+  int64_t ncs = 1;  // one thread per node of level j-1 (each writes up to 2^d level-j nodes)
+  for (int k = 0; k < d; ++k) ncs *= ((1 << j) / 2 + 1);
+  dim3 grid(blocks_for(ncs), nts);
+  const FastDiv f = make_fastdiv((unsigned)((1 << j) / 2 + 1));
   if (d == 1) k_comb_level<1><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
   else if (d == 2) k_comb_level<2><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
   else k_comb_level<3><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
@@ -830,7 +879,7 @@ void note_launches(int k) { count(k); }
 
 // explicit instantiations
 #define ST_INST(R)                                                                                                   \
-  template void launch_stencil<R>(int, const Geo&, const StencilCoef&, const R*, const cx<R>*, const cx<R>*, cx<R>*, \
+  template void launch_stencil<R>(int, const Geo&, const StencilCoefT<R>&, const R*, const cx<R>*, const cx<R>*, cx<R>*, \
                                   const cx<R>*, const CocgScal*, int, int64_t, double, cudaStream_t);                \
   template void launch_restrict<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,      \
                                    int64_t, cudaStream_t);                                                           \

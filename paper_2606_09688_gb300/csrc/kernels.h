@@ -15,12 +15,13 @@ struct CocgScal {
   double alpha_re, alpha_im;
   double beta_re, beta_im;
   double rr, bb;             // ||r||^2, ||b||^2
+  float alpha_f[2], beta_f[2];  // the same step lengths for FP32 kernels (no per-thread conversion)
   int active, iters, status, pad;
 };
 
 // y_q = op((K(c2) + lam_q M) x_q) for every active mode q of a level.
 template <typename R>
-void launch_stencil(int op, const Geo& g, const StencilCoef& sc, const R* c2, const cx<R>* x,
+void launch_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x,
                     const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
                     int64_t stride, double omega, cudaStream_t s);
 

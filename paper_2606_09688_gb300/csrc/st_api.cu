@@ -42,6 +42,7 @@ constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many t
 constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64
 constexpr double kThetaMG = 1.25;      // coarsest-grid resolution: k h_c <= theta
 constexpr double kOmega2D = 0.6, kOmega3D = 0.55, kOmega1D = 0.6;
+constexpr int kIterPerGraph = 4;  // COCG iterations between host convergence checks
 
 struct DevMem {
   std::vector<void*> ptrs;
@@ -112,6 +113,7 @@ struct MGLevel {
   int j = 0;
   Geo geo{};
   StencilCoef sc{};
+  StencilCoefT<float> scf{};
   std::vector<double> c2h;
   double* c2d = nullptr;
   float* c2f = nullptr;
@@ -212,6 +214,10 @@ struct Component {
   int* cerr = nullptr;
   int64_t d2h = 0;
   std::string err;
+  // CUDA graphs of the COCG start (init + first V-cycle) and of kIterPerGraph
+  // iterations, captured at setup on the component stream.
+  cudaGraphExec_t g_init = nullptr, g_iter = nullptr;
+  int64_t g_init_nodes = 0, g_iter_nodes = 0;
 };
 
 // Algorithmic flops per node of the complex Q1 stencil (K and M parts with
@@ -272,6 +278,8 @@ struct st_handle {
   ~st_handle() {
     if (scalar_h) cudaFreeHost(scalar_h);
     for (auto& c : comps) {
+      if (c->g_init) cudaGraphExecDestroy(c->g_init);
+      if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
       if (c->cscalar_h) cudaFreeHost(c->cscalar_h);
       if (c->cs) cudaStreamDestroy(c->cs);
       if (c->done) cudaEventDestroy(c->done);
@@ -734,6 +742,7 @@ st_status setup_component(st_handle* h, Component& c) {
     l0.j = c.jx;
     l0.geo = c.sl->geo;
     l0.sc = c.sl->sc;
+    l0.scf = to_float(l0.sc);
     l0.c2h = c.sl->c2h;
     l0.c2d = c.sl->c2d;
     l0.c2f = c.sl->c2f;
@@ -746,6 +755,7 @@ st_status setup_component(st_handle* h, Component& c) {
     double hh[3];
     for (int k = 0; k < p.d; ++k) hh[k] = (p.hi[k] - p.lo[k]) / (1 << j);
     l.sc = make_coef(p.d, hh);
+    l.scf = to_float(l.sc);
     l.c2h = average_c2(p.d, 1 << (j + 1), c.mg.back().c2h);
     l.c2d = h->upload(l.c2h);
     std::vector<float> cf(l.c2h.begin(), l.c2h.end());
@@ -774,6 +784,9 @@ st_status setup_component(st_handle* h, Component& c) {
 template <typename R> Work<R>& work_of(Component& c);
 template <> Work<double>& work_of<double>(Component& c) { return c.w64; }
 template <> Work<float>& work_of<float>(Component& c) { return c.w32; }
+template <typename R> const StencilCoefT<R>& coef_of(const MGLevel& l);
+template <> const StencilCoefT<double>& coef_of<double>(const MGLevel& l) { return l.sc; }
+template <> const StencilCoefT<float>& coef_of<float>(const MGLevel& l) { return l.scf; }
 template <typename R> const R* c2_of(const MGLevel& l);
 template <> const double* c2_of<double>(const MGLevel& l) { return l.c2d; }
 template <> const float* c2_of<float>(const MGLevel& l) { return l.c2f; }
@@ -880,11 +893,11 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const R* c2 = c2_of<R>(lv);
   const double cb = (double)lv.geo.ncells * rs;
   PROF(h, s, KC_JACOBI, m * n * 2 * cs + cb, m * n * 30.0,
-       launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, lv.sc, c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
+       launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, coef_of<R>(lv), c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
   PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
-       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
+       launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
   PROF(h, s, KC_MG_RESID, m * n * 3 * cs + cb, m * n * (fl + 2.0),
-       launch_stencil<R>(OP_RESID, lv.geo, lv.sc, c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
+       launch_stencil<R>(OP_RESID, lv.geo, coef_of<R>(lv), c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
   const MGLevel& lc = c.mg[l + 1];
   const double nc = (double)lc.geo.nnodes;
   PROF(h, s, KC_RESTRICT, m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
@@ -893,10 +906,83 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   PROF(h, s, KC_PROLONG, m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
        launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
   PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
-       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
+       launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
   PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
-       launch_stencil<R>(OP_JACOBI, lv.geo, lv.sc, c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
+       launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
   return xb;
+}
+
+double inner_tol(size_t rsize) { return rsize == 8 ? 1e-12 : 1e-5; }
+
+// COCG start: x = 0, r = g, z = B r, rho = r . z, p = z.
+template <typename R> void cocg_start(st_handle* h, Component& c) {
+  Work<R>& w = work_of<R>(c);
+  cudaStream_t s = c.cs;
+  const int64_t n = c.nx;
+  const double cs = sizeof(cx<R>);
+  const double tol = inner_tol(sizeof(R));
+  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  PROF(h, s, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
+       launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
+  cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
+  PROF(h, s, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
+       launch_dot<R>(2, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+  PROF(h, s, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
+}
+
+// One COCG iteration: w = A p, alpha, x += alpha p, r -= alpha w (modes that
+// converge are switched off on the device), z = B r, beta, p = z + beta p.
+template <typename R> void cocg_iteration(st_handle* h, Component& c) {
+  Work<R>& w = work_of<R>(c);
+  cudaStream_t s = c.cs;
+  const int64_t n = c.nx;
+  const double cs = sizeof(cx<R>), rs = sizeof(R);
+  const double tol = inner_tol(sizeof(R));
+  const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  const MGLevel& l0 = c.mg[0];
+  const R* c2 = c2_of<R>(l0);
+  const cx<R>* lam = lam_of<R>(*c.td);
+  const double fl = stencil_flops(l0.geo.d), cb = (double)l0.geo.ncells * rs;
+  const double m = c.nactive;
+  PROF(h, s, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
+       launch_stencil<R>(OP_APPLY, l0.geo, coef_of<R>(l0), c2, w.P, nullptr, w.Wv, lam, c.scal, c.nsel, n, 0.0, s));
+  PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+       launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+  PROF(h, s, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
+       launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+  cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
+  PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+       launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+  PROF(h, s, KC_UPDATE, m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+}
+
+// Capture the COCG start and kIterPerGraph iterations as CUDA graphs on the
+// component stream (every pointer and size is fixed after setup; modes that
+// converge are skipped on the device through their active flags).
+template <typename R> st_status capture_graphs(st_handle* h, Component& c) {
+  c.nactive = c.nsel;
+  for (int which = 0; which < 2; ++which) {
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = kernel_launch_count();
+    ST_CUDA(h, cudaStreamBeginCapture(c.cs, cudaStreamCaptureModeThreadLocal));
+    if (which == 0) cocg_start<R>(h, c);
+    else
+      for (int k = 0; k < kIterPerGraph; ++k) cocg_iteration<R>(h, c);
+    ST_CUDA(h, cudaStreamEndCapture(c.cs, &g));
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, ST_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+    const int64_t nodes = kernel_launch_count() - l0;
+    if (which == 0) {
+      c.g_init = ge;
+      c.g_init_nodes = nodes;
+    } else {
+      c.g_iter = ge;
+      c.g_iter_nodes = nodes;
+    }
+  }
+  return check_launch(h, "graph capture");
 }
 
 // Solve (lam_q M + K) x_q = g_q for every mode; w.G holds g, the result lands in w.X.
@@ -904,7 +990,7 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
   Work<R>& w = work_of<R>(c);
   cudaStream_t s = c.cs;
   const int64_t n = c.nx;
-  const double cs = sizeof(cx<R>), rs = sizeof(R);
+  const double cs = sizeof(cx<R>);
   iters_out = 0;
   c.nactive = c.nsel;
   if (c.direct) {
@@ -913,46 +999,31 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
          launch_band_solve<R>(w.band, w.bandG, c.bl, w.G, w.X, nullptr, c.nsel, n, c.cerr, s));
     return ccheck(c, "direct band solve");
   }
-  const double tol = sizeof(R) == 8 ? 1e-12 : 1e-5;
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
-  const MGLevel& l0 = c.mg[0];
-  const R* c2 = c2_of<R>(l0);
-  const cx<R>* lam = lam_of<R>(*c.td);
-  const double fl = stencil_flops(l0.geo.d), cb = (double)l0.geo.ncells * rs;
-  PROF(h, s, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
-       launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
-  // z = B r ; rho = r . z ; p = z
-  cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-  PROF(h, s, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
-       launch_dot<R>(2, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-  PROF(h, s, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
-  const int check_every = 4;
-  for (int it = 1; it <= max_iter; ++it) {
-    const double m = c.nactive;
-    PROF(h, s, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
-         launch_stencil<R>(OP_APPLY, l0.geo, l0.sc, c2, w.P, nullptr, w.Wv, lam, c.scal, c.nsel, n, 0.0, s));
-    PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
-         launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-    PROF(h, s, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
-         launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-    if (it % check_every == 0 || it == max_iter) {
-      ST_CUDAC(c, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
-      c.d2h += (int64_t)(c.nsel * sizeof(CocgScal));
-      ST_CUDAC(c, cudaStreamSynchronize(s));
-      st_status st = ccheck(c, "cocg");
-      if (st != ST_OK) return st;
-      int na = 0;
-      for (const auto& q : c.scal_h) na += q.active ? 1 : 0;
-      c.nactive = na;
-      if (na == 0) break;
-    }
-    z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-    PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
-         launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-    PROF(h, s, KC_UPDATE, m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+  const bool graphs = !h->prof_on && c.g_init != nullptr && c.g_iter != nullptr;
+  if (graphs) {
+    ST_CUDAC(c, cudaGraphLaunch(c.g_init, s));
+    note_launches((int)c.g_init_nodes);
+  } else {
+    cocg_start<R>(h, c);
   }
-  ST_CUDAC(c, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
-  ST_CUDAC(c, cudaStreamSynchronize(s));
+  for (int it = 0; it < max_iter; it += kIterPerGraph) {
+    if (graphs) {
+      ST_CUDAC(c, cudaGraphLaunch(c.g_iter, s));
+      note_launches((int)c.g_iter_nodes);
+    } else {
+      for (int k = 0; k < kIterPerGraph; ++k) cocg_iteration<R>(h, c);
+    }
+    ST_CUDAC(c, cudaMemcpyAsync(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost, s));
+    c.d2h += (int64_t)(c.nsel * sizeof(CocgScal));
+    ST_CUDAC(c, cudaStreamSynchronize(s));
+    st_status st = ccheck(c, "cocg");
+    if (st != ST_OK) return st;
+    int na = 0;
+    for (const auto& q : c.scal_h) na += q.active ? 1 : 0;
+    c.nactive = na;
+    if (na == 0) break;
+  }
   int worst = 0;
   for (const auto& q : c.scal_h) {
     iters_out = std::max(iters_out, q.iters);
@@ -1088,6 +1159,10 @@ st_status setup_context(st_handle* h, Component& c) {
   if (c.method == 0) {
     st_status s = c.inner64 ? prepare_work<double>(h, c) : prepare_work<float>(h, c);
     if (s != ST_OK) return s;
+    if (!c.direct) {
+      s = c.inner64 ? capture_graphs<double>(h, c) : capture_graphs<float>(h, c);
+      if (s != ST_OK) return s;
+    }
   }
   return ST_OK;
 }
