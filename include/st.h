@@ -154,9 +154,10 @@ st_status st_kernel_launches(const st_handle* h, int64_t* count);
  * recording a CUDA event pair on the handle's stream around every kernel
  * launch (extra launch overhead: use it for a separate measurement pass);
  * st_profile(h, 0) stops.  st_profile_read synchronises and writes one
- * entry per kernel class seen since the last st_profile call (at most
- * max_out; *n_out receives the count): launches, summed event time, and the
- * algorithmic bytes and flops of those launches. */
+ * entry per kernel class and grid size seen since the last st_profile call,
+ * named "<class>@<unknowns of the grid>" (at most max_out; *n_out receives
+ * the count): launches, summed event time, and the algorithmic bytes and
+ * flops of those launches. */
 typedef struct {
   char name[32];
   int64_t launches;

@@ -454,6 +454,162 @@ __global__ void __launch_bounds__(32) k_band_solve_p2(const cx<R>* __restrict__ 
   }
 }
 
+// FP64 variant of the fixed-slot solve: GB300 issues FP64 at a small
+// fraction of the FP32 rate per SM sub-partition, so one warp per mode is
+// bound by the FP64 pipe of its sub-partition.  Here each of SLOTS warps owns
+// one register slot (lanes hold rows r with (r mod bw) / 32 = warp), so the
+// per-row complex FMAs of a mode spread over SLOTS sub-partitions; the
+// finished row is passed through shared memory with one block barrier per row.
+// (ybuf is written by other threads between the barriers, so it must not be a
+// restrict pointer: that would let the compiler reuse an earlier load of it.)
+template <typename R, int SLOTS, int PASS, int SG>
+__device__ __forceinline__ void band_group32_mw(const cx<R>* __restrict__ st, int c, int nrow, int ld, int lane,
+                                                int warp, cx<R>& v, const cx<R>& bcur, cx<R>& y,
+                                                cx<R>* ybuf, cx<R>* __restrict__ dst) {
+  constexpr int bw = 32 * SLOTS;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const cx<R>* row = st + (size_t)(PASS == 0 ? i : 31 - i) * ld;
+    if (warp == SG && lane == i) {
+      const int kp = 32 * c + i;
+      const int k = PASS == 0 ? kp : nrow - 1 - kp;
+      dst[k] = PASS == 0 ? y * row[0] : y;
+    }
+    if (warp == SG) {
+      const int t = lane - i + (lane <= i ? bw : 0);
+      const cx<R> a = row[t];
+      const cx<R> base = lane == i ? bcur : v;
+      v = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, base.re)), fma(-a.re, y.im, fma(-a.im, y.re, base.im)));
+    } else {
+      const int d = (warp - SG + SLOTS) % SLOTS;
+      const cx<R> a = row[lane - i + 32 * d];
+      v = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, v.re)), fma(-a.re, y.im, fma(-a.im, y.re, v.im)));
+    }
+    const int nslot = (i < 31) ? SG : (SG + 1) % SLOTS;
+    if (warp == nslot && lane == ((i + 1) & 31)) ybuf[i & 1] = v;
+    __syncthreads();
+    y = ybuf[i & 1];
+  }
+}
+
+template <typename R, int SLOTS>
+__global__ void __launch_bounds__(32 * SLOTS) k_band_solve_mw(const cx<R>* __restrict__ F, const cx<R>* __restrict__ G,
+                                                              BandLayout L, const cx<R>* __restrict__ b,
+                                                              cx<R>* __restrict__ x, const CocgScal* __restrict__ scal,
+                                                              int64_t vstride, int* err) {
+  constexpr int C = 32, bw = 32 * SLOTS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = blockIdx.x;
+  if (scal != nullptr && !scal[q].active) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ld = L.ld, nrow = (int)L.nrow;
+  const size_t stage_elems = (size_t)C * ld;
+  cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem);
+  cx<R>* stage1 = stage0 + stage_elems;
+  cx<R>* ybuf = stage1 + stage_elems;  // 2 entries
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ybuf + 2);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  unsigned phase[2] = {0u, 0u};
+  const int nchunks = (nrow + C - 1) / C;
+  cx<R>* dst = x + (int64_t)q * vstride;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    const cx<R>* Mq = (pass == 0 ? F : G) + (int64_t)q * L.mstride;
+    const cx<R>* src = pass == 0 ? b + (int64_t)q * vstride : dst;
+    auto chunk = [&](int c, int& klo, int& cnt) {
+      const int k0 = c * C;
+      cnt = min(C, nrow - k0);
+      klo = pass == 0 ? k0 : nrow - k0 - cnt;
+    };
+    auto issue = [&](int c) {
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      cx<R>* st = (c & 1) ? stage1 : stage0;
+      const unsigned bytes = (unsigned)((size_t)cnt * ld * sizeof(cx<R>));
+      mbar_expect_tx(&bar[c & 1], bytes);
+      bulk_g2s(st, Mq + (int64_t)klo * ld, bytes, &bar[c & 1]);
+    };
+    auto at = [&](int rp) -> cx<R> {
+      if (rp >= nrow) return zero;
+      return src[pass == 0 ? rp : nrow - 1 - rp];
+    };
+    if (threadIdx.x == 0) {
+      issue(0);
+      if (nchunks > 1) issue(1);
+    }
+    cx<R> v = at(lane + 32 * warp);
+    cx<R> bcur = at(lane + bw), bnext = at(C + lane + bw);
+    if (threadIdx.x == 0) ybuf[1] = v;  // row 0 (lane 0 of warp 0)
+    __syncthreads();
+    cx<R> y = ybuf[1];
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      phase[c & 1] ^= 1u;
+      const cx<R> bnn = at((c + 2) * C + lane + bw);
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      const cx<R>* st = (c & 1) ? stage1 : stage0;
+      const int sg = c % SLOTS;
+      if (cnt == C) {
+#define ST_MW_GROUP(P, S)                                                                            \
+  if (sg == S) band_group32_mw<R, SLOTS, P, (S < SLOTS ? S : 0)>(st, c, nrow, ld, lane, warp, v, bcur, y, \
+                                                                  ybuf, dst);
+        if (pass == 0) {
+          ST_MW_GROUP(0, 0) ST_MW_GROUP(0, 1) ST_MW_GROUP(0, 2) ST_MW_GROUP(0, 3)
+        } else {
+          ST_MW_GROUP(1, 0) ST_MW_GROUP(1, 1) ST_MW_GROUP(1, 2) ST_MW_GROUP(1, 3)
+        }
+#undef ST_MW_GROUP
+      } else {
+        for (int i = 0; i < cnt; ++i) {
+          const cx<R>* row = st + (size_t)(pass == 0 ? i : cnt - 1 - i) * ld;
+          if (warp == sg && lane == i) {
+            const int kp = 32 * c + i;
+            const int k = pass == 0 ? kp : nrow - 1 - kp;
+            dst[k] = pass == 0 ? y * row[0] : y;
+          }
+          int t;
+          cx<R> base = v;
+          if (warp == sg) {
+            t = lane - i + (lane <= i ? bw : 0);
+            if (lane == i) base = bcur;
+          } else {
+            t = lane - i + 32 * ((warp - sg + SLOTS) % SLOTS);
+          }
+          const cx<R> a = row[t];
+          v = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, base.re)), fma(-a.re, y.im, fma(-a.im, y.re, base.im)));
+          const int nslot = (i < 31) ? sg : (sg + 1) % SLOTS;
+          if (warp == nslot && lane == ((i + 1) & 31)) ybuf[i & 1] = v;
+          __syncthreads();
+          y = ybuf[i & 1];
+        }
+      }
+      bcur = bnext;
+      bnext = bnn;
+      __syncthreads();
+      if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 2);
+        for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
+      }
+      return;
+    }
+    __syncthreads();
+  }
+}
+
 std::mutex g_attr_mu;  // launches come from several host threads (one per component)
 
 template <typename R, int SLOTS> void set_smem_attr(size_t bytes) {
@@ -461,6 +617,15 @@ template <typename R, int SLOTS> void set_smem_attr(size_t bytes) {
   std::lock_guard<std::mutex> lock(g_attr_mu);
   if (bytes > done) {
     cudaFuncSetAttribute(k_band_solve_w<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
+template <typename R, int SLOTS> void set_smem_attr_mw(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_solve_mw<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done = bytes;
   }
 }
@@ -510,6 +675,19 @@ bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, cons
                        const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s) {
   // power-of-two bandwidths (the 2D grids): fixed-slot kernel with 32-row chunks
   const size_t smem32 = 2 * (size_t)32 * L.ld * sizeof(cx<R>) + 2 * sizeof(uint64_t);
+  if (sizeof(R) == 8 && smem32 + 2 * sizeof(cx<R>) <= 160 * 1024 && (L.bw == 64 || L.bw == 128)) {
+    // FP64: spread each mode over bw / 32 warps (one FP64 pipe per warp)
+    const size_t sm = smem32 + 2 * sizeof(cx<R>);
+    if (L.bw == 64) {
+      set_smem_attr_mw<R, 2>(sm);
+      k_band_solve_mw<R, 2><<<nmodes, 64, sm, s>>>(F, G, L, b, x, scal, vstride, err);
+    } else {
+      set_smem_attr_mw<R, 4>(sm);
+      k_band_solve_mw<R, 4><<<nmodes, 128, sm, s>>>(F, G, L, b, x, scal, vstride, err);
+    }
+    note_launches(1);
+    return true;
+  }
   if (smem32 <= 160 * 1024 && (L.bw == 32 || L.bw == 64 || L.bw == 128)) {
     if (L.bw == 32) {
       set_smem_attr_p2<R, 1>(smem32);

@@ -257,6 +257,7 @@ struct st_handle {
   // stream around every launch, with the algorithmic bytes and flops of it.
   struct ProfRec {
     int cls;
+    int64_t size;  // unknowns of the grid the launch works on
     cudaEvent_t a, b;
     double bytes, flops;
   };
@@ -350,10 +351,11 @@ struct ProfScope {
   st_handle* h;
   cudaStream_t s;
   int cls;
+  int64_t size;
   double bytes, flops;
   cudaEvent_t a = nullptr;
-  ProfScope(st_handle* h_, cudaStream_t s_, int cls_, double bytes_, double flops_)
-      : h(h_), s(s_), cls(cls_), bytes(bytes_), flops(flops_) {
+  ProfScope(st_handle* h_, cudaStream_t s_, int cls_, int64_t size_, double bytes_, double flops_)
+      : h(h_), s(s_), cls(cls_), size(size_), bytes(bytes_), flops(flops_) {
     if (h->prof_on) {
       std::lock_guard<std::mutex> lock(h->prof_mu);
       a = h->get_event();
@@ -365,14 +367,14 @@ struct ProfScope {
       std::lock_guard<std::mutex> lock(h->prof_mu);
       cudaEvent_t b = h->get_event();
       cudaEventRecord(b, s);
-      h->prof.push_back({cls, a, b, bytes, flops});
+      h->prof.push_back({cls, size, a, b, bytes, flops});
     }
   }
 };
-#define PROF(h, s, cls, bytes, flops, call) \
-  do {                                     \
-    ProfScope ps_(h, s, cls, bytes, flops); \
-    call;                                  \
+#define PROF(h, s, cls, size, bytes, flops, call) \
+  do {                                           \
+    ProfScope ps_(h, s, cls, size, bytes, flops); \
+    call;                                        \
   } while (0)
 
 st_status check_launch(st_handle* h, const char* where) {
@@ -885,29 +887,29 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const double m = (double)c.nactive, cs = sizeof(cx<R>), rs = sizeof(R);
   const double fl = stencil_flops(lv.geo.d);
   if (l == L) {
-    PROF(h, s, KC_BAND_SOLVE, m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
+    PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
          launch_band_solve<R>(w.band, w.bandG, c.bl, b, xb, c.scal, c.nsel, n, c.cerr, s));
     return xb;
   }
   const double om = omega_of(lv.geo.d);
   const R* c2 = c2_of<R>(lv);
   const double cb = (double)lv.geo.ncells * rs;
-  PROF(h, s, KC_JACOBI, m * n * 2 * cs + cb, m * n * 30.0,
+  PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 2 * cs + cb, m * n * 30.0,
        launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, coef_of<R>(lv), c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, s, KC_MG_RESID, m * n * 3 * cs + cb, m * n * (fl + 2.0),
+  PROF(h, s, KC_MG_RESID, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 2.0),
        launch_stencil<R>(OP_RESID, lv.geo, coef_of<R>(lv), c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
   const MGLevel& lc = c.mg[l + 1];
   const double nc = (double)lc.geo.nnodes;
-  PROF(h, s, KC_RESTRICT, m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
+  PROF(h, s, KC_RESTRICT, (int64_t)(n), m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
        launch_restrict<R>(lv.geo, lc.geo, rtmp, w.bl[l + 1], c.scal, c.nsel, n, lc.geo.nnodes, s));
   cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
-  PROF(h, s, KC_PROLONG, m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
+  PROF(h, s, KC_PROLONG, (int64_t)(n), m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
        launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
-  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
-  PROF(h, s, KC_JACOBI, m * n * 3 * cs + cb, m * n * (fl + 30.0),
+  PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
   return xb;
 }
@@ -922,12 +924,12 @@ template <typename R> void cocg_start(st_handle* h, Component& c) {
   const double cs = sizeof(cx<R>);
   const double tol = inner_tol(sizeof(R));
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
-  PROF(h, s, KC_REDUCE, c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
+  PROF(h, s, KC_REDUCE, (int64_t)(n), c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
        launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
   cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-  PROF(h, s, KC_REDUCE, c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
+  PROF(h, s, KC_REDUCE, (int64_t)(n), c.nactive * (double)n * 2 * cs, c.nactive * (double)n * 8.0,
        launch_dot<R>(2, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-  PROF(h, s, KC_UPDATE, c.nactive * (double)n * 2 * cs, 0.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
+  PROF(h, s, KC_UPDATE, (int64_t)(n), c.nactive * (double)n * 2 * cs, 0.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 1, s));
 }
 
 // One COCG iteration: w = A p, alpha, x += alpha p, r -= alpha w (modes that
@@ -944,16 +946,16 @@ template <typename R> void cocg_iteration(st_handle* h, Component& c) {
   const cx<R>* lam = lam_of<R>(*c.td);
   const double fl = stencil_flops(l0.geo.d), cb = (double)l0.geo.ncells * rs;
   const double m = c.nactive;
-  PROF(h, s, KC_STENCIL, m * n * 2 * cs + cb, m * n * fl,
+  PROF(h, s, KC_STENCIL, (int64_t)(n), m * n * 2 * cs + cb, m * n * fl,
        launch_stencil<R>(OP_APPLY, l0.geo, coef_of<R>(l0), c2, w.P, nullptr, w.Wv, lam, c.scal, c.nsel, n, 0.0, s));
-  PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+  PROF(h, s, KC_REDUCE, (int64_t)(n), m * n * 2 * cs, m * n * 8.0,
        launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-  PROF(h, s, KC_UPDATE, m * n * 6 * cs, m * n * 12.0,
+  PROF(h, s, KC_UPDATE, (int64_t)(n), m * n * 6 * cs, m * n * 12.0,
        launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
   cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
-  PROF(h, s, KC_REDUCE, m * n * 2 * cs, m * n * 8.0,
+  PROF(h, s, KC_REDUCE, (int64_t)(n), m * n * 2 * cs, m * n * 8.0,
        launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
-  PROF(h, s, KC_UPDATE, m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+  PROF(h, s, KC_UPDATE, (int64_t)(n), m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
 }
 
 // Capture the COCG start and kIterPerGraph iterations as CUDA graphs on the
@@ -995,7 +997,7 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
   c.nactive = c.nsel;
   if (c.direct) {
     const double m = c.nsel;
-    PROF(h, s, KC_BAND_SOLVE, m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
+    PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
          launch_band_solve<R>(w.band, w.bandG, c.bl, w.G, w.X, nullptr, c.nsel, n, c.cerr, s));
     return ccheck(c, "direct band solve");
   }
@@ -1036,7 +1038,7 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
 
 st_status assemble_rhs(st_handle* h, Component& c) {
   if (c.f_ready) return ST_OK;
-  PROF(h, c.cs, KC_RHS, (double)(h->nterm_rows + c.nt) * c.nx * 8.0, 2.0 * h->nterm_rows * c.nt * (double)c.nx,
+  PROF(h, c.cs, KC_RHS, (int64_t)(c.nx), (double)(h->nterm_rows + c.nt) * c.nx * 8.0, 2.0 * h->nterm_rows * c.nt * (double)c.nx,
        launch_rhs_assemble(c.td->rhs_coef, c.sl->loads, c.F, h->nterm_rows, c.nt, c.nx, c.cs));
   if (c.Fg_all != nullptr)
     for (int i = 0; i < c.nt; ++i)
@@ -1047,7 +1049,7 @@ st_status assemble_rhs(st_handle* h, Component& c) {
 }
 
 st_status read_norm(st_handle* h, Component& c, const double* v, int64_t n, double& out) {
-  PROF(h, c.cs, KC_NORM, (double)n * 8.0, 2.0 * n, launch_norm2(v, n, c.cpart, c.cscalar, c.cs));
+  PROF(h, c.cs, KC_NORM, (int64_t)(n), (double)n * 8.0, 2.0 * n, launch_norm2(v, n, c.cpart, c.cscalar, c.cs));
   int serr = 0;
   ST_CUDAC(c, cudaMemcpyAsync(&serr, c.cerr, sizeof(int), cudaMemcpyDeviceToHost, c.cs));
   ST_CUDAC(c, cudaMemcpyAsync(c.cscalar_h, c.cscalar, sizeof(double), cudaMemcpyDeviceToHost, c.cs));
@@ -1061,22 +1063,22 @@ st_status read_norm(st_handle* h, Component& c, const double* v, int64_t n, doub
 template <typename R> st_status sweep_time_eig(st_handle* h, Component& c, const double* Rin, int& iters) {
   Work<R>& w = work_of<R>(c);
   const double cs = sizeof(cx<R>), nx = (double)c.nx;
-  PROF(h, c.cs, KC_TRANSFORM, c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+  PROF(h, c.cs, KC_TRANSFORM, (int64_t)(c.nx), c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
        launch_fwd_transform<R>(c.td->W, Rin, w.G, c.nsel, c.nt, c.nx, c.cs));
   st_status s = inner_solve<R>(h, c, iters);
   if (s != ST_OK) return s;
-  PROF(h, c.cs, KC_TRANSFORM, 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
+  PROF(h, c.cs, KC_TRANSFORM, (int64_t)(c.nx), 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
        launch_back_transform<R>(c.td->V, c.td->wq, w.X, c.U, c.nsel, c.nt, c.nx, c.cs));
   return ccheck(c, "time transforms");
 }
 
 st_status sweep_space_eig(st_handle* h, Component& c, const double* Rin) {
   const double nx = (double)c.nx, nt = c.nt;
-  PROF(h, c.cs, KC_SPACE_EIG, (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+  PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
        launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, c.cs));
-  PROF(h, c.cs, KC_SPACE_EIG, (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
+  PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
        launch_time_band_solve(c.ab, c.piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
-  PROF(h, c.cs, KC_SPACE_EIG, (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
+  PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
        launch_gemm_right(c.KU, c.PhiT, c.U, c.nt, c.nx, 1, 1, c.cs));
   return ccheck(c, "space eigenbasis sweep");
 }
@@ -1116,7 +1118,7 @@ st_status solve_one(st_handle* h, Component& c) {
     }
     c.info.sweeps = sw + 1;
     c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
-    PROF(h, c.cs, KC_RESIDUAL64, 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
+    PROF(h, c.cs, KC_RESIDUAL64, (int64_t)(c.nx), 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
          (double)n * (4.0 * ipow3(c.sl->geo.d) + 20.0),
          launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, c.U, c.F, c.td->Aband, c.td->Bband, c.KU, c.MU, c.Rv, c.nt,
                          c.cs));
@@ -1431,7 +1433,7 @@ st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
     int64_t nsp = 1;
     for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
     const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
-    PROF(h, h->stream, KC_COMBINE, outb + inb, (double)nsp * nts * (2.0 * (1 << p.d) + 8.0 * (c1 - c0)),
+    PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, (double)nsp * nts * ((Yp ? 2.0 : 0.0) + 4.0 * (c1 - c0)),
          launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
   }
   return check_launch(h, "combine");
@@ -1486,22 +1488,25 @@ st_status st_profile(st_handle* h, int enable) {
 st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n_out) {
   if (!h || !n_out) return ST_ERR_ARG;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
-  st_kernel_stat agg[KC_COUNT];
-  std::memset(agg, 0, sizeof(agg));
+  for (auto& c : h->comps)
+    if (cudaStreamSynchronize(c->cs) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+  // one entry per (kernel class, grid size): the class name with "@<unknowns>"
+  std::map<std::pair<int, int64_t>, st_kernel_stat> agg;
   for (auto& r : h->prof) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return fail(h, ST_ERR_CUDA, "event timing failed");
-    agg[r.cls].launches += 1;
-    agg[r.cls].ms += ms;
-    agg[r.cls].bytes += r.bytes;
-    agg[r.cls].flops += r.flops;
+    st_kernel_stat& s = agg[std::make_pair(r.cls, r.size)];
+    s.launches += 1;
+    s.ms += ms;
+    s.bytes += r.bytes;
+    s.flops += r.flops;
   }
   int n = 0;
-  for (int k = 0; k < KC_COUNT; ++k) {
-    if (agg[k].launches == 0) continue;
+  for (auto& kv : agg) {
     if (out && n < max_out) {
-      out[n] = agg[k];
-      std::snprintf(out[n].name, sizeof(out[n].name), "%s", kClassName[k]);
+      out[n] = kv.second;
+      std::snprintf(out[n].name, sizeof(out[n].name), "%s@%lld", kClassName[kv.first.first],
+                    (long long)kv.first.second);
     }
     ++n;
   }

@@ -268,11 +268,11 @@ class Solver:
         self._check(self._lib.st_profile(self._h, 1 if enable else 0))
 
     def profile_read(self) -> List[dict]:
-        buf = (StKernelStat * 32)()
+        buf = (StKernelStat * 512)()
         n = C.c_int()
-        self._check(self._lib.st_profile_read(self._h, buf, 32, C.byref(n)))
+        self._check(self._lib.st_profile_read(self._h, buf, 512, C.byref(n)))
         return [dict(name=buf[i].name.decode(), launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
-                     flops=buf[i].flops) for i in range(min(n.value, 32))]
+                     flops=buf[i].flops) for i in range(min(n.value, 512))]
 
     def transfer_bytes(self):
         """(host->device, device->host) bytes moved by the library so far."""

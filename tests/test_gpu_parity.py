@@ -97,6 +97,12 @@ def test_layered_medium_2d_multigrid(prec):
     _run(W.layered_2d(8, 2), prec, (6, 6))
 
 
+def test_layered_medium_2d_level9_fp64_direct_127():
+    """n = 9: the (7,2) component (127^2 grid, half bandwidth 128) is solved by the
+    banded direct method; in FP64 each mode spreads over four warps."""
+    _run(W.layered_2d(9, 2), 0, (7, 7), method="schur")
+
+
 def test_layered_medium_2d_level10():
     """n = 10: (8,2) 255^2 x 5 with a 4-level V-cycle; (2,8) with the space eigenbasis."""
     _run(W.layered_2d(10, 2), 1, (8, 8), method="schur", check_components=False)
