@@ -122,6 +122,63 @@ __global__ void k_band_ldlt(cx<R>* __restrict__ F, BandLayout L, int* err) {
   }
 }
 
+// The same factorisation with the active window in shared memory: column c
+// of the trailing matrix (rows c..c+bw) lives in slot c mod P, P = bw + 1,
+// entry t at win[slot * P + t].  At column k every pair 1 <= j <= i <= m
+// takes a_{k+i,k+j} -= (a_{k+i,k} / d_k) a_{k+j,k}; thread (i, p) owns row
+// offset i and the column offsets j = 1 + p, 1 + p + NP, ..., so a warp
+// (consecutive i, one j) reads and writes consecutive words of one slot.
+// Then column k leaves for global memory (as L and 1/d_k) and column k + P
+// (untouched so far: no column before k + 1 reaches it) enters its slot.
+template <typename R>
+__global__ void k_band_ldlt_win(cx<R>* __restrict__ F, BandLayout L, int RI, int NP, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* win = reinterpret_cast<cx<R>*>(smem_raw);
+  const int q = blockIdx.x;
+  const int bw = L.bw, ld = L.ld, P = bw + 1;
+  const int64_t nrow = L.nrow;
+  cx<R>* Fq = F + (int64_t)q * L.mstride;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int i = 1 + tid % RI, p = tid / RI;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int e = tid; e < P * P; e += nth) {
+    const int c = e / P, t = e - (e / P) * P;
+    win[e] = (c < nrow && c + t < nrow) ? Fq[(int64_t)c * ld + t] : zero;
+  }
+  __syncthreads();
+  int slot0 = 0;  // k mod P
+  for (int64_t k = 0; k < nrow; ++k) {
+    const cx<R>* colk = win + slot0 * P;
+    const cx<R> d = colk[0];
+    if (!(d.re * d.re + d.im * d.im > R(0))) {
+      if (tid == 0) atomicExch(err, 1);
+      return;
+    }
+    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
+    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
+    if (i <= m) {
+      const cx<R> u = colk[i] * dinv;
+      for (int j = 1 + p; j <= i; j += NP) {
+        int sj = slot0 + j;
+        if (sj >= P) sj -= P;
+        cx<R>& tgt = win[sj * P + (i - j)];
+        const cx<R> a = colk[j];
+        tgt = mk<R>(fma(-u.re, a.re, fma(u.im, a.im, tgt.re)), fma(-u.re, a.im, fma(-u.im, a.re, tgt.im)));
+      }
+    }
+    __syncthreads();
+    // column k of L (with 1/d_k in place of the unit diagonal) to global
+    // memory, and column k + P into the freed slot (entry t by one thread)
+    const int64_t c = k + P;
+    for (int t = tid; t < P; t += nth) {
+      if (t <= m) Fq[k * ld + t] = t == 0 ? dinv : colk[t] * dinv;
+      win[slot0 * P + t] = (c < nrow && c + t < nrow) ? Fq[c * ld + t] : zero;
+    }
+    __syncthreads();
+    slot0 = slot0 + 1 == P ? 0 : slot0 + 1;
+  }
+}
+
 template <typename R>
 __global__ void k_band_rows(const cx<R>* __restrict__ F, cx<R>* __restrict__ G, BandLayout L) {
   const int q = blockIdx.y;
@@ -639,6 +696,17 @@ template <typename R, int SLOTS> void set_smem_attr_p2(size_t bytes) {
   }
 }
 
+constexpr size_t kMaxWindowBytes = 200 * 1024;
+
+template <typename R> void set_smem_attr_ldlt(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_ldlt_win<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
 }  // namespace
 
 BandLayout band_layout(int64_t nrow, int bw) {
@@ -659,7 +727,15 @@ void launch_band_form(const double* Kb, const double* Mb, const cx<double>* lam,
 
 template <typename R>
 void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int* err, cudaStream_t s) {
-  k_band_ldlt<R><<<nmodes, 256, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, err);
+  const size_t P = (size_t)L.bw + 1, win_bytes = P * P * sizeof(cx<R>);
+  if (win_bytes <= kMaxWindowBytes) {
+    // window in shared memory: RI row lanes (bw rounded up to a warp multiple) x NP column phases
+    const int RI = (L.bw + 31) / 32 * 32, NP = RI >= 256 ? 1 : 256 / RI;
+    set_smem_attr_ldlt<R>(win_bytes);
+    k_band_ldlt_win<R><<<nmodes, RI * NP, win_bytes, s>>>(F, L, RI, NP, err);
+  } else {
+    k_band_ldlt<R><<<nmodes, 256, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, err);
+  }
   k_band_rows<R><<<dim3(blocks_for(L.nrow * L.ld), nmodes), kBlock, 0, s>>>(F, G, L);
   note_launches(2);
 }

@@ -88,60 +88,113 @@ template <int D> __device__ __forceinline__ bool neighbour(const int i[3], int s
 }
 
 // ------------------------------------------------------------------ stencils
-template <int D, typename R, int OP>
+__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
+
+// s * a / b with one reciprocal of |b|^2 (two divisions in the textbook form).
+template <typename R> __device__ __forceinline__ cx<R> scaled_div(R s, cx<R> a, cx<R> b) {
+  const R w = s * rcp_rn(fma(b.re, b.re, b.im * b.im));
+  return mk<R>(w * fma(a.re, b.re, a.im * b.im), w * fma(a.im, b.re, -a.re * b.im));
+}
+
+// One thread per interior node and MQ time modes: the node's row of the
+// stiffness (c^2 cell sums times the element entries) and its neighbour
+// offsets are formed once and applied to every mode of the group, so the
+// per-mode cost is the 3^D loads and the complex FMAs.
+template <int D, typename R, int OP, int MQ>
 __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
                                                     const cx<R>* __restrict__ x, const cx<R>* __restrict__ b,
                                                     cx<R>* __restrict__ y, const cx<R>* __restrict__ lam,
-                                                    const CocgScal* __restrict__ scal, int64_t stride, R omega) {
-  const int q = blockIdx.y;
-  if (scal != nullptr && !scal[q].active) return;
+                                                    const CocgScal* __restrict__ scal, int nmodes, int64_t stride,
+                                                    R omega) {
+  const int q0 = blockIdx.y * MQ;
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= g.nnodes) return;
   constexpr int NS = ipow3(D), CEN = (NS - 1) / 2;
   int i[3] = {0, 0, 0};
   decode<D>(a, g, i);
-  R S[NS];
-  cell_sums<D, R>(c2, g.N, i, S);
-  const cx<R> l = lam[q];
-  const cx<R> diag = fma_s(sc.mtot[CEN], l, mk<R>(S[CEN] * sc.ke[CEN], R(0)));
-  const int64_t base = (int64_t)q * stride;
-  if (OP == OP_JACOBI_ZERO) {
-    y[base + a] = omega * cdiv(b[base + a], diag);
-    return;
-  }
-  cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
+  R kr[NS];
+  cell_sums<D, R>(c2, g.N, i, kr);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    int64_t off;
-    if (neighbour<D>(i, s, g.n, off)) {
-      const cx<R> v = x[base + a + off];
-      ak = fma_s(S[s] * sc.ke[s], v, ak);
-      am = fma_s(sc.mtot[s], v, am);
+  for (int s = 0; s < NS; ++s) kr[s] *= sc.ke[s];
+  int off[NS];
+  unsigned valid = 0u;
+  if (OP != OP_JACOBI_ZERO) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      int64_t o;
+      if (neighbour<D>(i, s, g.n, o)) valid |= 1u << s;
+      off[s] = (int)o;
     }
   }
-  const cx<R> Ax = fma_c(l, am, ak);
-  if (OP == OP_APPLY) {
-    y[base + a] = Ax;
-  } else if (OP == OP_RESID) {
-    y[base + a] = b[base + a] - Ax;
-  } else {  // OP_JACOBI
-    const cx<R> xo = x[base + a];
-    y[base + a] = xo + omega * cdiv(b[base + a] - Ax, diag);
+#pragma unroll
+  for (int m = 0; m < MQ; ++m) {
+    const int q = q0 + m;
+    if (q >= nmodes) break;
+    if (scal != nullptr && !scal[q].active) continue;
+    const cx<R> l = lam[q];
+    const cx<R> diag = fma_s(sc.mtot[CEN], l, mk<R>(kr[CEN], R(0)));
+    const int64_t base = (int64_t)q * stride + a;
+    if (OP == OP_JACOBI_ZERO) {
+      y[base] = scaled_div(omega, b[base], diag);
+      continue;
+    }
+    cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if ((valid >> s) & 1u) {
+        const cx<R> v = x[base + off[s]];
+        ak = fma_s(kr[s], v, ak);
+        am = fma_s(sc.mtot[s], v, am);
+      }
+    }
+    const cx<R> Ax = fma_c(l, am, ak);
+    if (OP == OP_APPLY) {
+      y[base] = Ax;
+    } else if (OP == OP_RESID) {
+      y[base] = b[base] - Ax;
+    } else {  // OP_JACOBI
+      const cx<R> xo = x[base];
+      y[base] = xo + scaled_div(omega, b[base] - Ax, diag);
+    }
   }
 }
 
+template <int D, typename R, int MQ>
+void stencil_dispatch_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                         cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
+                         cudaStream_t s) {
+  dim3 grid(blocks_for(g.nnodes), (nmodes + MQ - 1) / MQ);
+  const R om = (R)omega;
+  switch (op) {
+    case OP_APPLY:
+      k_stencil<D, R, OP_APPLY, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      break;
+    case OP_RESID:
+      k_stencil<D, R, OP_RESID, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      break;
+    case OP_JACOBI:
+      k_stencil<D, R, OP_JACOBI, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      break;
+    default:
+      k_stencil<D, R, OP_JACOBI_ZERO, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      break;
+  }
+}
+
+// Modes per thread: up to four (two for the 27-point 3D stencil), fewer when
+// the grid alone would not fill the GPU twice over.
 template <int D, typename R>
 void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                       cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
                       cudaStream_t s) {
-  dim3 grid(blocks_for(g.nnodes), nmodes);
-  const R om = (R)omega;
-  switch (op) {
-    case OP_APPLY: k_stencil<D, R, OP_APPLY><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
-    case OP_RESID: k_stencil<D, R, OP_RESID><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
-    case OP_JACOBI: k_stencil<D, R, OP_JACOBI><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
-    default: k_stencil<D, R, OP_JACOBI_ZERO><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, stride, om); break;
-  }
+  constexpr int MQMAX = D == 3 ? 2 : 4;
+  const int64_t blocks = (int64_t)blocks_for(g.nnodes);
+  int mq = 1;
+  while (mq < MQMAX && mq < nmodes && blocks * ((nmodes + 2 * mq - 1) / (2 * mq)) >= 2 * 152) mq *= 2;
+  if (mq == 4) stencil_dispatch_mq<D, R, (MQMAX >= 4 ? 4 : 1)>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+  else if (mq == 2) stencil_dispatch_mq<D, R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+  else stencil_dispatch_mq<D, R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
 }
 
 // --------------------------------------------------------- multigrid transfer
@@ -612,12 +665,21 @@ __global__ void k_time_band_solve(const double* __restrict__ ab, const int* __re
 // Level by level, Y_j = P Y_{j-1} + sum_{components at level j} c_k u_k(., t_s),
 // on all nodes of level j (boundary included, for the lift by u0); a component
 // finer than the target level is injected (its nodes contain the target nodes).
-template <int D> __device__ __forceinline__ double comp_value(const CombComp& cc, int j, const int P[3], int s,
-                                                              int nts, int c, const double* __restrict__ tbv,
-                                                              const int* __restrict__ tspan, bool interior) {
+// Sign flip on the integer pipe: FP64 issue slots are the scarce resource of
+// the combination kernel on this GPU, so neither the sign of a coefficient
+// nor a power-of-two scale costs an FP64 instruction there.
+__device__ __forceinline__ double with_sign(double x, unsigned sign_hi) {
+  return __hiloint2double(__double2hiint(x) ^ (int)sign_hi, __double2loint(x));
+}
+
+// v + coef * (component value at level-j node P, target time s), three FP64
+// FMAs per node; coef = -1 enters as a sign flip of the B-spline values.
+template <int D> __device__ __forceinline__ double comp_add(const CombComp& cc, int j, const int P[3], int s,
+                                                            int nts, int c, const double* __restrict__ tbv,
+                                                            const int* __restrict__ tspan, bool interior, double v) {
   const int sh = cc.jx - j;  // >= 0: injection from a finer component grid
   const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
-  double val = 0.0;
+  const unsigned sg = cc.coef > 0 ? 0u : 0x80000000u;
   if (interior) {
     int64_t ii = 0, si = 1, nx = 1;
 #pragma unroll
@@ -631,7 +693,9 @@ template <int D> __device__ __forceinline__ double comp_value(const CombComp& cc
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       const int row = span + t - 1;
-      if (row >= 0 && row < nt) val = fma(tb[t], cc.U[(int64_t)row * nx + ii], val);
+      const bool ok = row >= 0 && row < nt;
+      const double u = ok ? cc.U[(int64_t)row * nx + ii] : 0.0;
+      v = fma(with_sign(tb[t], sg), u, v);
     }
   }
   if (cc.lift != nullptr) {
@@ -641,17 +705,33 @@ template <int D> __device__ __forceinline__ double comp_value(const CombComp& cc
       ia += (int64_t)(P[k] << sh) * sa;
       sa *= (N + 1);
     }
-    val += cc.lift[ia];
+    v += with_sign(cc.lift[ia], sg);
   }
-  return val;
+  return v;
+}
+
+// x / 2 for the prolongation midpoints as an exponent decrement of the high
+// word (integer pipe): exact whenever the half is a normal number; a half in
+// the subnormal range (|x| < 2^-1021) flushes to a signed zero, and infinities
+// and NaNs pass unchanged.
+__device__ __forceinline__ double half_of(double x) {
+  int hi = __double2hiint(x), lo = __double2loint(x);
+  const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+  if (ex - 2u < 0x7fdu) {
+    hi -= 0x100000;
+  } else if (ex < 2u) {
+    hi &= (int)0x80000000u;
+    lo = 0;
+  }
+  return __hiloint2double(hi, lo);
 }
 
 // One thread per node Q of level j-1 (all nodes, boundary included): it
 // produces the level-j nodes P = 2Q + e, e in {0,1}^d (those inside the grid).
 // Their prolongated values are formed separably, direction by direction
 // (value at the odd node = half the sum of its two coarse neighbours), so
-// each fine node costs about two FP64 operations; the components of this
-// level are then added node by node.  Without Yprev (the coarsest level of
+// each fine node costs about one FP64 addition; the components of this level
+// are then added node by node.  Without Yprev (the coarsest level of
 // the combination) only the components are evaluated.
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __restrict__ Yprev,
@@ -703,7 +783,7 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
     for (int k = 0; k < D; ++k) {
 #pragma unroll
       for (int e = 0; e < NE; ++e)
-        if ((e >> k) & 1) f[e] = 0.5 * (f[e ^ (1 << k)] + f[e]);
+        if ((e >> k) & 1) f[e] = half_of(f[e ^ (1 << k)] + f[e]);
     }
   }
 #pragma unroll
@@ -721,11 +801,7 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
     }
     if (!inside) continue;
     double v = f[e];
-    for (int c = c0; c < c1; ++c) {
-      const CombComp cc = comps[c];
-      const double val = comp_value<D>(cc, j, P, s, nts, c, tbv, tspan, interior);
-      v = cc.coef > 0 ? v + val : v - val;
-    }
+    for (int c = c0; c < c1; ++c) v = comp_add<D>(comps[c], j, P, s, nts, c, tbv, tspan, interior, v);
     Y[(int64_t)s * nsp + pidx] = v;
   }
 }

@@ -810,8 +810,11 @@ st_status ccheck(Component& c, const char* where) {
   return ST_OK;
 }
 
-// Workspace and coarsest-level factorisations of a time-eigenbasis component
-// (setup time, on the handle's stream).
+// Workspace and coarsest-level factorisations of a time-eigenbasis component.
+// The factorisations run on the component's own stream (after the uploads on
+// the handle's stream), so that those of different components overlap with
+// each other and with the host work of the components set up after it; the
+// zero-pivot flag they leave in c.cerr is read at the end of st_setup.
 template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   Work<R>& w = work_of<R>(c);
   if (w.ready) return ST_OK;
@@ -855,15 +858,12 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   w.bandG = h->alloc<cx<R>>((size_t)c.nsel * c.bl.mstride);
   ST_NEED(h, w.band);
   ST_NEED(h, w.bandG);
-  launch_band_form<R>(c.Kb, c.Mb, c.td->lam64, w.band, c.bl, c.nsel, h->stream);
-  ST_CUDA(h, cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
-  launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, h->dev_err, h->stream);
-  int herr = 0;
-  ST_CUDA(h, cudaMemcpyAsync(&herr, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+  ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
+  launch_band_form<R>(c.Kb, c.Mb, c.td->lam64, w.band, c.bl, c.nsel, c.cs);
+  launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, c.cerr, c.cs);
   st_status s = check_launch(h, "band factorisation");
   if (s != ST_OK) return s;
-  if (herr) return fail(h, ST_ERR_NUMERIC, "zero pivot in a banded LDL^T factorisation");
   w.ready = true;
   return ST_OK;
 }
@@ -1293,6 +1293,21 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   if (cudaStreamSynchronize(hp->stream) != cudaSuccess) {
     g_create_error = "stream synchronisation failed during setup";
     return ST_ERR_CUDA;
+  }
+  // the factorisations enqueued on the component streams: wait, then read
+  // their zero-pivot flags and clear them for the solves
+  for (auto& c : hp->comps) {
+    if (c->cs == nullptr || c->cerr == nullptr) continue;
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, c->cerr, sizeof(int), cudaMemcpyDeviceToHost, c->cs) != cudaSuccess ||
+        cudaStreamSynchronize(c->cs) != cudaSuccess) {
+      g_create_error = "stream synchronisation failed during setup";
+      return ST_ERR_CUDA;
+    }
+    if (herr != 0) {
+      g_create_error = "zero pivot in a banded LDL^T factorisation";
+      return ST_ERR_NUMERIC;
+    }
   }
   *out = h.release();
   return ST_OK;
