@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"],
                     help="precision of the headline value; the other one is reported beside it")
     ap.add_argument("--skip", default="", help="comma list of: other,profile,e2e,cpu")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="inner Krylov tolerance per refinement sweep (0 = library default)")
+    ap.add_argument("--max-direct-rows", type=int, default=0,
+                    help="largest spatial grid solved by the banded direct method (0 = library default)")
     ap.add_argument("--only-component", type=int, default=-1,
                     help="profiling aid: each step solves only this component (no combination)")
     return ap.parse_args()
@@ -266,6 +270,8 @@ def run_ours(args):
     nsp = ((1 << target[0]) + 1) ** problem.d
     nts = (1 << target[1]) + 1
     out = torch.empty((nts, nsp), dtype=torch.float64, device=dev)
+    # pinned host buffer for the end-to-end measurement, allocated once up front
+    host_out = None if "e2e" in skip else torch.empty((nts, nsp), dtype=torch.float64, pin_memory=True)
 
     def barrier():
         torch.cuda.synchronize()
@@ -285,7 +291,8 @@ def run_ours(args):
         code = ST_FP64 if prec == "fp64" else ST_FP32_IR
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
-            solver = Solver(problem, precision=code, stream=stream)
+            solver = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
+                            max_direct_rows=args.max_direct_rows)
             setup_s = time.perf_counter() - t0
             dofs = solver.total_dofs
             for _ in range(args.warmup):
@@ -310,8 +317,9 @@ def run_ours(args):
             comp_ms = None
             if "profile" not in skip:
                 solver.profile(True)
-                solver.solve(-1, sync=False)
-                solver.combine(target[0], target[1], out)
+                solver.solve(args.only_component, sync=False)
+                if args.only_component < 0:
+                    solver.combine(target[0], target[1], out)
                 stats = solver.profile_read()
                 solver.profile(False)
                 # each component alone (what bounds the step when they overlap)
@@ -336,27 +344,48 @@ def run_ours(args):
     if "e2e" not in skip:
         for r in results.values():
             r["solver"].close()
-        host_out = torch.empty((nts, nsp), dtype=torch.float64, pin_memory=True)
         code = ST_FP64 if args.precision == "fp64" else ST_FP32_IR
         e2e_steps = max(1, min(args.steps, 2))
+        # one untimed pass first: the pinned output buffer's pages are mapped
+        # for the GPU on its first copy
+        with torch.cuda.stream(stream):
+            s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
+                            max_direct_rows=args.max_direct_rows)
+            s.solve(-1, sync=False)
+            s.combine(target[0], target[1], out)
+            host_out.copy_(out, non_blocking=True)
+            stream.synchronize()
+            s.close()
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
+        phase = [0.0, 0.0, 0.0, 0.0]  # setup, solve + combine, copy to host, release
         for _ in range(e2e_steps):
             with torch.cuda.stream(stream):
-                s = Solver(problem, precision=code, stream=stream)
+                ta = time.perf_counter()
+                s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
+                            max_direct_rows=args.max_direct_rows)
+                tb = time.perf_counter()
                 s.solve(-1, sync=False)
                 s.combine(target[0], target[1], out)
+                stream.synchronize()
+                tc = time.perf_counter()
                 host_out.copy_(out, non_blocking=True)
                 stream.synchronize()
+                td = time.perf_counter()
                 a, b = s.transfer_bytes()
                 h2d += a
                 d2h += b + host_out.numel() * 8
                 s.close()
+                te = time.perf_counter()
+                for k, dt in enumerate((tb - ta, tc - tb, td - tc, te - td)):
+                    phase[k] += dt / e2e_steps
         e2e_s = maxall((time.perf_counter() - t0) / e2e_steps)
         e2e = {"value": head["dofs"] * world / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "s_per_step": e2e_s,
-               "includes": "st_setup from host callbacks + solve + combine + target grid copied to pinned host"}
+               "includes": "st_setup from host callbacks + solve + combine + target grid copied to pinned host",
+               "phases_s": {"setup": phase[0], "solve_combine": phase[1], "copy_to_host": phase[2],
+                            "release": phase[3]}}
     if rank != 0:
         return
     cpu = None if "cpu" in skip else cpu_baseline(args.workload)

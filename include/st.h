@@ -95,6 +95,13 @@ typedef struct {
   int max_iter;     /* inner Krylov iteration limit per mode (0 = default) */
   int max_sweeps;   /* refinement sweeps per component (0 = default) */
   void* stream;     /* cudaStream_t */
+  double inner_tol; /* relative residual at which a mode's inner Krylov solve
+                       stops within one refinement sweep (0 = default: 1e-12
+                       for FP64 inner solves, 1e-4 for FP32) */
+  int max_direct_rows;  /* spatial grids with at most this many unknowns
+                           (and a band of at most 256) are solved by the
+                           banded direct method, larger ones by multigrid-
+                           preconditioned COCG (0 = default 16384) */
 } st_options;
 
 typedef struct {

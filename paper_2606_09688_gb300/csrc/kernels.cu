@@ -3,6 +3,7 @@
 // Every kernel works on the uniform Q1 grids of one spatial level (see Geo
 // in common.cuh).  Complex vectors of the time eigenbasis are stored
 // mode-major: element (q, a) at q * stride + a.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -563,6 +564,70 @@ __global__ void __launch_bounds__(kBlock) k_stencil_real2(Geo g, StencilCoef sc,
   }
 }
 
+// FP64 space-time residual R = F - (A (x) M + B (x) K) U in one pass: one
+// thread per interior node and chunk of time rows [jb, je) forms its
+// stiffness row and neighbour offsets once, then streams over the time rows
+// j = jb-2 .. je+1, applying K and M to U_j and adding A(i, j) M U_j +
+// B(i, j) K U_j to the five rows i = j-2 .. j+2 that row j reaches (A, B
+// pentadiagonal); row j-2 is complete after step j.  Chunks (the grid's y)
+// only matter for small grids with many time rows; they recompute the two
+// rows of halo on either side.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_residual_fused(Geo g, StencilCoef sc, const double* __restrict__ c2,
+                                                           const double* __restrict__ U,
+                                                           const double* __restrict__ F,
+                                                           const double* __restrict__ Aband,
+                                                           const double* __restrict__ Bband,
+                                                           double* __restrict__ Rout, int nt, int chunk) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  const int jb = blockIdx.y * chunk, je = min(nt, jb + chunk);
+  const int64_t nx = g.nnodes;
+  constexpr int NS = ipow3(D);
+  int i[3] = {0, 0, 0};
+  decode<D>(a, g, i);
+  double kr[NS];
+  cell_sums<D, double>(c2, g.N, i, kr);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) kr[s] *= sc.ke[s];
+  int off[NS];
+  unsigned valid = 0u;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int64_t o;
+    if (neighbour<D>(i, s, g.n, o)) valid |= 1u << s;
+    off[s] = (int)o;
+  }
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // rows j-2 .. j+2
+  for (int j = max(0, jb - 2); j <= je + 1; ++j) {
+    if (j < nt) {
+      const double* uj = U + (int64_t)j * nx + a;
+      double ku = 0.0, mu = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if ((valid >> s) & 1u) {
+          const double v = uj[off[s]];
+          ku = fma(kr[s], v, ku);
+          mu = fma(sc.mtot[s], v, mu);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const int r = j - 2 + k;  // A(r, j) sits at Aband[r * 5 + (j - r) + 2]
+        if (r >= 0 && r < nt) {
+          const int e = r * 5 + 4 - k;
+          acc[k] = fma(-__ldg(Aband + e), mu, fma(-__ldg(Bband + e), ku, acc[k]));
+        }
+      }
+    }
+    const int done = j - 2;
+    if (done >= jb && done < je) Rout[(int64_t)done * nx + a] = F[(int64_t)done * nx + a] + acc[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = acc[k + 1];
+    acc[4] = 0.0;
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_time_combine(const double* __restrict__ Aband,
                                                          const double* __restrict__ Bband,
                                                          const double* __restrict__ F, const double* __restrict__ KU,
@@ -806,6 +871,46 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
   }
 }
 
+// ------------------------------------------------- dense coarse-level solve
+// x_q = Ainv_q b_q: b_q staged in shared memory, one warp per row (coalesced
+// row reads, lanes over columns), warp-shuffle reduction of the dot product.
+constexpr int kDenseRowsPerBlock = 32;
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_dense_mv(const cx<R>* __restrict__ Ainv, int n,
+                                                     const cx<R>* __restrict__ b, cx<R>* __restrict__ x,
+                                                     const CocgScal* __restrict__ scal, int64_t vstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* bs = reinterpret_cast<cx<R>*>(smem_raw);
+  const int q = blockIdx.y;
+  if (scal != nullptr && !scal[q].active) return;
+  const cx<R>* bq = b + (int64_t)q * vstride;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) bs[c] = bq[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const cx<R>* Aq = Ainv + (int64_t)q * n * n;
+  const int r1 = min(n, (int)(blockIdx.x + 1) * kDenseRowsPerBlock);
+  for (int r = blockIdx.x * kDenseRowsPerBlock + warp; r < r1; r += kBlock / 32) {
+    const cx<R>* row = Aq + (int64_t)r * n;
+    R re = R(0), im = R(0);
+    for (int c = lane; c < n; c += 32) {
+      const cx<R> a = row[c], v = bs[c];
+      re = fma(a.re, v.re, fma(-a.im, v.im, re));
+      im = fma(a.re, v.im, fma(a.im, v.re, im));
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) x[(int64_t)q * vstride + r] = mk<R>(re, im);
+  }
+}
+
+template <typename R> __global__ void k_identity(cx<R>* __restrict__ I, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int64_t j = e / n, r = e - (e / n) * n;
+  I[e] = mk<R>(r == j ? R(1) : R(0), R(0));
+}
+
 }  // namespace
 
 // ================================================================ wrappers
@@ -895,12 +1000,19 @@ void launch_back_transform(const cx<double>* V, const double* wq, const cx<R>* X
 void launch_residual(const Geo& g, const StencilCoef& sc, const double* c2, const double* U, const double* F,
                      const double* Aband, const double* Bband, double* KU, double* MU, double* Rout, int nt,
                      cudaStream_t s) {
-  count(2);
-  dim3 grid(blocks_for(g.nnodes), nt);
-  if (g.d == 1) k_stencil_real2<1, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
-  else if (g.d == 2) k_stencil_real2<2, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
-  else k_stencil_real2<3, false><<<grid, kBlock, 0, s>>>(g, sc, c2, U, KU, MU, 0, 0, g.nnodes, g.nnodes, 0);
-  k_time_combine<<<grid, kBlock, 0, s>>>(Aband, Bband, F, KU, MU, Rout, nt, g.nnodes);
+  count(1);
+  (void)KU;
+  (void)MU;
+  // time chunks of at least 8 rows, as many as it takes to give the grid
+  // about two CTAs per SM
+  const unsigned bx = blocks_for(g.nnodes);
+  int nch = (int)std::min<int64_t>((nt + 7) / 8, (304 + (int64_t)bx - 1) / bx);
+  nch = std::max(nch, 1);
+  const int chunk = (nt + nch - 1) / nch;
+  const dim3 grid(bx, (nt + chunk - 1) / chunk);
+  if (g.d == 1) k_residual_fused<1><<<grid, kBlock, 0, s>>>(g, sc, c2, U, F, Aband, Bband, Rout, nt, chunk);
+  else if (g.d == 2) k_residual_fused<2><<<grid, kBlock, 0, s>>>(g, sc, c2, U, F, Aband, Bband, Rout, nt, chunk);
+  else k_residual_fused<3><<<grid, kBlock, 0, s>>>(g, sc, c2, U, F, Aband, Bband, Rout, nt, chunk);
 }
 
 void launch_norm2(const double* v, int64_t n, double* part, double* out, cudaStream_t s) {
@@ -950,6 +1062,19 @@ void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps,
   else k_comb_level<3><<<grid, kBlock, 0, s>>>(j, Yprev, comps, c0, c1, tbv, tspan, nts, Y, f);
 }
 
+template <typename R>
+void launch_dense_coarse(const cx<R>* Ainv, int64_t n, const cx<R>* b, cx<R>* x, const CocgScal* scal, int nmodes,
+                         int64_t vstride, cudaStream_t s) {
+  count(1);
+  const dim3 grid((unsigned)((n + kDenseRowsPerBlock - 1) / kDenseRowsPerBlock), nmodes);
+  k_dense_mv<R><<<grid, kBlock, n * sizeof(cx<R>), s>>>(Ainv, (int)n, b, x, scal, vstride);
+}
+
+template <typename R> void launch_identity(cx<R>* I, int64_t n, cudaStream_t s) {
+  count(1);
+  k_identity<R><<<blocks_for(n * n), kBlock, 0, s>>>(I, n);
+}
+
 int64_t kernel_launch_count() { return g_launches.load(); }
 void note_launches(int k) { count(k); }
 
@@ -970,7 +1095,10 @@ void note_launches(int k) { count(k); }
   template void launch_update_p<R>(cx<R>*, const cx<R>*, const CocgScal*, int, int64_t, int64_t, int, cudaStream_t);      \
   template void launch_fwd_transform<R>(const cx<double>*, const double*, cx<R>*, int, int, int64_t, cudaStream_t);  \
   template void launch_back_transform<R>(const cx<double>*, const double*, const cx<R>*, double*, int, int, int64_t, \
-                                         cudaStream_t);
+                                         cudaStream_t);                                                              \
+  template void launch_dense_coarse<R>(const cx<R>*, int64_t, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,   \
+                                       cudaStream_t);                                                                \
+  template void launch_identity<R>(cx<R>*, int64_t, cudaStream_t);
 ST_INST(double)
 ST_INST(float)
 #undef ST_INST

@@ -92,6 +92,15 @@ struct CombComp {
 void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,
                        const int* tspan, int nts, double* Y, cudaStream_t s);
 
+// Coarsest multigrid level by an explicit inverse (grids of at most a few
+// thousand unknowns): x_q = Ainv_q b_q for every active mode, Ainv_q the
+// n x n inverse of mode q at q * n * n (row r contiguous).
+template <typename R>
+void launch_dense_coarse(const cx<R>* Ainv, int64_t n, const cx<R>* b, cx<R>* x, const CocgScal* scal, int nmodes,
+                         int64_t vstride, cudaStream_t s);
+// I (n x n identity, column j at j * n): right-hand sides of the inversion.
+template <typename R> void launch_identity(cx<R>* I, int64_t n, cudaStream_t s);
+
 // Kernels launched by this process through the wrappers above.
 int64_t kernel_launch_count();
 void note_launches(int k);

@@ -15,7 +15,9 @@
 // U = C Phi^T.
 // Both are wrapped in FP64 iterative refinement on R = F - (A (x) M + B (x) K) U.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -36,6 +38,7 @@ using namespace st;
 namespace {
 
 constexpr int kMaxDirectRows = 16384;  // largest grid solved by the banded direct method
+constexpr int64_t kMaxDenseCoarse = 1024;  // coarsest multigrid grids up to this size use an explicit inverse
 constexpr int kMaxBandWidth = 256;     // widest band the warp solve supports
 constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
 constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
@@ -160,6 +163,7 @@ template <typename R> struct Work {
   std::vector<cx<R>*> bl, rl, xa, xb;  // per MG level l >= 1
   cx<R>* band = nullptr;               // F factors, nsel x mstride
   cx<R>* bandG = nullptr;              // G (rows of L), nsel x mstride
+  cx<R>* cinv = nullptr;               // coarsest-level inverses, nsel x n x n (small coarse grids)
   bool ready = false;
 };
 
@@ -340,12 +344,12 @@ st_status fail(st_handle* h, st_status code, const std::string& msg) {
 
 enum KClass {
   KC_STENCIL = 0, KC_JACOBI, KC_MG_RESID, KC_RESTRICT, KC_PROLONG, KC_BAND_SOLVE, KC_REDUCE, KC_UPDATE,
-  KC_TRANSFORM, KC_RESIDUAL64, KC_NORM, KC_RHS, KC_SPACE_EIG, KC_COMBINE, KC_SETUP, KC_COUNT
+  KC_TRANSFORM, KC_RESIDUAL64, KC_NORM, KC_RHS, KC_SPACE_EIG, KC_COMBINE, KC_SETUP, KC_DENSE_COARSE, KC_COUNT
 };
 const char* const kClassName[KC_COUNT] = {"stencil_apply", "jacobi_smooth", "mg_residual", "mg_restrict",
                                           "mg_prolong", "band_solve", "cocg_reduce", "cocg_update",
                                           "time_transform", "st_residual_fp64", "norm_fp64", "rhs_assemble",
-                                          "space_eigenbasis", "combine_level", "setup"};
+                                          "space_eigenbasis", "combine_level", "setup", "coarse_inverse"};
 
 struct ProfScope {
   st_handle* h;
@@ -595,19 +599,22 @@ st_status setup_time_level(st_handle* h, int jt, TimeData& td) {
 
 // Coarsest multigrid level of a time-eigenbasis component: the coarsest grid
 // must resolve the largest wave number k = sqrt(-Re lam / min c^2) of its
-// modes (k h_c <= theta); grids with at most kMaxDirectRows unknowns are
-// solved directly.
-int choose_coarse(const st_problem& p, const Component& c) {
+// modes (k h_c <= theta); grids with at most max_direct unknowns (default
+// kMaxDirectRows) are solved directly.
+int choose_coarse(const st_problem& p, const Component& c, int64_t max_direct) {
   double kmax = 0.0;
   for (int q = 0; q < c.td->eig.nsel; ++q)
     kmax = std::max(kmax, std::sqrt(std::max(0.0, -c.td->eig.lam[q].real()) / c.sl->c2min));
   double L = 0.0;
   for (int k = 0; k < p.d; ++k) L = std::max(L, p.hi[k] - p.lo[k]);
+  // no coarser than the largest grid that the explicit coarse inverse takes:
+  // below it, extra levels only add launches to every V-cycle
   int jc = 2;
+  while (jc + 1 < c.jx && make_geo(p.d, jc + 1).nnodes <= kMaxDenseCoarse) ++jc;
   while (jc < c.jx && kmax * L / (1 << jc) > kThetaMG) ++jc;
   auto fits = [&](int j) {
     const Geo g = make_geo(p.d, j);
-    return g.nnodes <= kMaxDirectRows && band_width(g) <= kMaxBandWidth;
+    return g.nnodes <= max_direct && band_width(g) <= kMaxBandWidth;
   };
   if (fits(c.jx)) return c.jx;  // the banded direct solve beats a V-cycle with a large coarse grid
   int jmax = 1;                 // largest level the banded solve handles
@@ -735,7 +742,7 @@ st_status setup_component(st_handle* h, Component& c) {
   // time eigenbasis
   c.nsel = c.td->eig.nsel;
   c.inner64 = (h->opt.precision == ST_FP64) || (c.td->eig.cond_est > kKappaFP32);
-  c.jc = choose_coarse(p, c);
+  c.jc = choose_coarse(p, c, h->opt.max_direct_rows > 0 ? (int64_t)h->opt.max_direct_rows : kMaxDirectRows);
   c.direct = (c.jc == c.jx);
   // multigrid hierarchy jx -> jc (level 0 uses the sampled c^2)
   c.mg.clear();
@@ -862,6 +869,21 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
   launch_band_form<R>(c.Kb, c.Mb, c.td->lam64, w.band, c.bl, c.nsel, c.cs);
   launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, c.cerr, c.cs);
+  if (!c.direct && c.bl.nrow <= kMaxDenseCoarse) {
+    // multigrid coarsest level: explicit inverses, column j = the banded
+    // solve of e_j (all columns of one mode in one launch, factor shared)
+    const int64_t nc = c.bl.nrow;
+    cx<R>* ident = h->alloc<cx<R>>((size_t)(nc * nc));
+    w.cinv = h->alloc<cx<R>>((size_t)(c.nsel * nc * nc));
+    ST_NEED(h, ident);
+    ST_NEED(h, w.cinv);
+    launch_identity<R>(ident, nc, c.cs);
+    BandLayout shared = c.bl;
+    shared.mstride = 0;
+    for (int q = 0; q < c.nsel; ++q)
+      launch_band_solve<R>(w.band + (int64_t)q * c.bl.mstride, w.bandG + (int64_t)q * c.bl.mstride, shared, ident,
+                           w.cinv + (int64_t)q * nc * nc, nullptr, (int)nc, nc, c.cerr, c.cs);
+  }
   st_status s = check_launch(h, "band factorisation");
   if (s != ST_OK) return s;
   w.ready = true;
@@ -887,8 +909,13 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const double m = (double)c.nactive, cs = sizeof(cx<R>), rs = sizeof(R);
   const double fl = stencil_flops(lv.geo.d);
   if (l == L) {
-    PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
-         launch_band_solve<R>(w.band, w.bandG, c.bl, b, xb, c.scal, c.nsel, n, c.cerr, s));
+    if (w.cinv != nullptr) {
+      PROF(h, s, KC_DENSE_COARSE, (int64_t)(n), m * (double)n * (n + 2.0) * cs, m * (double)n * n * 8.0,
+           launch_dense_coarse<R>(w.cinv, n, b, xb, c.scal, c.nsel, n, s));
+    } else {
+      PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs),
+           m * (double)n * c.bw * 16.0, launch_band_solve<R>(w.band, w.bandG, c.bl, b, xb, c.scal, c.nsel, n, c.cerr, s));
+    }
     return xb;
   }
   const double om = omega_of(lv.geo.d);
@@ -914,7 +941,13 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   return xb;
 }
 
-double inner_tol(size_t rsize) { return rsize == 8 ? 1e-12 : 1e-5; }
+double inner_tol(const st_handle* h, size_t rsize) {
+  if (h->opt.inner_tol > 0.0) return h->opt.inner_tol;
+  // FP32: each sweep gains about four digits whatever the inner tolerance
+  // (the FP32 representation of the correction limits it), so a loose
+  // inner solve costs fewer iterations for the same number of sweeps
+  return rsize == 8 ? 1e-12 : 1e-4;
+}
 
 // COCG start: x = 0, r = g, z = B r, rho = r . z, p = z.
 template <typename R> void cocg_start(st_handle* h, Component& c) {
@@ -922,7 +955,7 @@ template <typename R> void cocg_start(st_handle* h, Component& c) {
   cudaStream_t s = c.cs;
   const int64_t n = c.nx;
   const double cs = sizeof(cx<R>);
-  const double tol = inner_tol(sizeof(R));
+  const double tol = inner_tol(h, sizeof(R));
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
   PROF(h, s, KC_REDUCE, (int64_t)(n), c.nsel * (double)n * 3 * cs, c.nsel * (double)n * 4.0,
        launch_cocg_init<R>(w.G, w.X, w.Rr, c.scal, c.part, c.nsel, n, n, s));
@@ -939,7 +972,7 @@ template <typename R> void cocg_iteration(st_handle* h, Component& c) {
   cudaStream_t s = c.cs;
   const int64_t n = c.nx;
   const double cs = sizeof(cx<R>), rs = sizeof(R);
-  const double tol = inner_tol(sizeof(R));
+  const double tol = inner_tol(h, sizeof(R));
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
   const MGLevel& l0 = c.mg[0];
   const R* c2 = c2_of<R>(l0);
@@ -1169,6 +1202,24 @@ st_status setup_context(st_handle* h, Component& c) {
   return ST_OK;
 }
 
+// Host-side phase times of st_setup, printed to stderr when the environment
+// variable ST_SETUP_TRACE is set (diagnostics only).
+struct SetupTrace {
+  bool on = std::getenv("ST_SETUP_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  std::map<std::string, double> acc;
+  void mark(const char* phase) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    acc[phase] += std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+  }
+  ~SetupTrace() {
+    if (!on) return;
+    for (const auto& kv : acc) std::fprintf(stderr, "st_setup %-28s %9.2f ms\n", kv.first.c_str(), kv.second);
+  }
+};
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -1177,6 +1228,7 @@ extern "C" {
 st_status st_setup(const st_problem* problem, const st_options* options, st_handle** out) {
   if (out == nullptr || problem == nullptr) return fail(nullptr, ST_ERR_ARG, "null argument");
   *out = nullptr;
+  SetupTrace trace;
   const st_problem& p = *problem;
   if (p.d < 1 || p.d > 3) return fail(nullptr, ST_ERR_ARG, "d must be 1, 2 or 3");
   if (!(p.T > 0.0) || !std::isfinite(p.T)) return fail(nullptr, ST_ERR_ARG, "T must be positive");
@@ -1193,10 +1245,14 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   if (options) h->opt = *options;
   if (h->opt.precision != ST_FP64 && h->opt.precision != ST_FP32_IR)
     return fail(nullptr, ST_ERR_ARG, "unknown precision");
+  if (!(h->opt.inner_tol >= 0.0 && h->opt.inner_tol < 1.0) || !(h->opt.tol >= 0.0 && h->opt.tol < 1.0))
+    return fail(nullptr, ST_ERR_ARG, "tolerances must lie in [0, 1)");
+  if (h->opt.max_direct_rows < 0) return fail(nullptr, ST_ERR_ARG, "max_direct_rows must be >= 0");
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->nterm_rows = p.n_terms + 2;
   h->launches0 = kernel_launch_count();
   st_handle* hp = h.get();
+  trace.mark("validation");
   hp->part = hp->alloc<double>(304);
   hp->scalar = hp->alloc<double>(1);
   hp->dev_err = hp->alloc<int>(1);
@@ -1234,6 +1290,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
         return s;
       }
       hp->space[jx] = std::move(sl);
+      trace.mark("space levels");
     }
     const int nt = (1 << jt) + 1;
     const int64_t nx = make_geo(p.d, jx).nnodes;
@@ -1246,6 +1303,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
         return s;
       }
       hp->time[jt] = std::move(td);
+      trace.mark("time levels");
     }
     TimeData& td = *hp->time[jt];
     if (!space_eig && !td.have_eig) {
@@ -1273,6 +1331,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
         g_create_error = "device allocation failed";
         return ST_ERR_OOM;
       }
+      trace.mark("time eigenbasis");
     }
     auto c = std::make_unique<Component>();
     c->jx = jx;
@@ -1282,7 +1341,9 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
     c->sl = hp->space[jx].get();
     c->td = &td;
     st_status s = setup_component(hp, *c);
+    trace.mark("component data");
     if (s == ST_OK) s = setup_context(hp, *c);
+    trace.mark("component context");
     if (s != ST_OK) {
       g_create_error = hp->err;
       hp->comps.push_back(std::move(c));  // released with the handle
@@ -1294,6 +1355,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
     g_create_error = "stream synchronisation failed during setup";
     return ST_ERR_CUDA;
   }
+  trace.mark("handle stream sync");
   // the factorisations enqueued on the component streams: wait, then read
   // their zero-pivot flags and clear them for the solves
   for (auto& c : hp->comps) {
@@ -1309,6 +1371,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
       return ST_ERR_NUMERIC;
     }
   }
+  trace.mark("component stream sync");
   *out = h.release();
   return ST_OK;
 }

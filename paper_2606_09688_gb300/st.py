@@ -43,7 +43,7 @@ class StProblem(C.Structure):
 
 class StOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("max_sweeps", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("inner_tol", C.c_double), ("max_direct_rows", C.c_int)]
 
 
 class StComponentInfo(C.Structure):
@@ -145,7 +145,7 @@ class Solver:
     """One problem instance behind the C ABI (st_setup .. st_destroy)."""
 
     def __init__(self, problem, precision: int = ST_FP64, tol: float = 0.0, max_iter: int = 0,
-                 max_sweeps: int = 0, stream=None):
+                 max_sweeps: int = 0, stream=None, inner_tol: float = 0.0, max_direct_rows: int = 0):
         import torch
         self._lib = lib()
         p = problem
@@ -183,7 +183,8 @@ class Solver:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        opt = StOptions(precision, tol, max_iter, max_sweeps, C.c_void_p(stream.cuda_stream))
+        opt = StOptions(precision, tol, max_iter, max_sweeps, C.c_void_p(stream.cuda_stream), inner_tol,
+                        max_direct_rows)
         h = C.c_void_p()
         code = self._lib.st_setup(C.byref(prob), C.byref(opt), C.byref(h))
         if code != ST_OK:

@@ -108,3 +108,28 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu():
     prob.mx = 1
     assert L.st_setup(C.byref(prob), None, C.byref(h)) == B.ST_ERR_ARG   # no c^2 callback
     assert h.value is None
+
+
+def test_setup_rejects_bad_tolerances_without_touching_the_gpu():
+    from paper_2606_09688_gb300 import st as B
+    L = B.lib()
+    prob = B.StProblem()
+    prob.d = 1
+    prob.hi[0] = 1.0
+    prob.T = 1.0
+    prob.J = 2
+    prob.mx = 1
+    prob.mt = 1
+
+    def c2(n, x, out, user):
+        for i in range(n):
+            out[i] = 1.0
+        return 0
+    cb = B.SPACE_FN(c2)
+    prob.c2.fn = cb
+    h = C.c_void_p()
+    for tol, inner in ((-1e-3, 0.0), (1.5, 0.0), (0.0, -1.0), (0.0, 1.0), (0.0, float("nan"))):
+        opt = B.StOptions(B.ST_FP64, tol, 0, 0, None, inner, 0)
+        assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
+        assert b"tolerances" in L.st_last_error(None)
+        assert h.value is None
