@@ -212,3 +212,61 @@ def batch_instances(count: int = 64, seed: int = 0, levels: Sequence[int] = (8, 
                            name=f"batch_{i}_n{n}", **levels_nm(n, m)))
     return out
 
+
+
+@dataclass
+class InverseSetup:
+    """Inputs of the receiver-misfit gradient: a base problem (box, T, levels),
+    c^2 and the source's spatial factor as nodal values on the uniform
+    parameter grid of level jp, the source's time factor, receivers, the target
+    time level of the misfit, and c^2 of the synthetic observations."""
+    base: Problem
+    jp: int
+    c2_nodal: np.ndarray
+    g_nodal: np.ndarray
+    s: TimeFn
+    receivers: np.ndarray
+    jt_star: int
+    c2_obs_nodal: np.ndarray
+
+
+def param_nodes(d: int, jp: int) -> np.ndarray:
+    """All (2^jp+1)^d nodes of the unit box, x fastest."""
+    ax = np.linspace(0.0, 1.0, (1 << jp) + 1)
+    mesh = np.meshgrid(*([ax] * d), indexing="ij")[::-1]
+    return np.stack([m.ravel() for m in mesh], axis=1)
+
+
+def smooth_field(d: int, seed: int, lo: float = 0.5, hi: float = 2.0, n_modes: int = 6,
+                 kmax: int = 2) -> SpaceFn:
+    """lo + (hi - lo) (1 + tanh(g)) / 2 with g = sum_k a_k cos(2 pi kappa_k . x + phi_k),
+    kappa_k integers in [-kmax, kmax]^d without 0, a_k ~ N(0, 1); default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    kap = []
+    while len(kap) < n_modes:
+        k = rng.integers(-kmax, kmax + 1, size=d)
+        if np.any(k != 0):
+            kap.append(k)
+    kap = np.asarray(kap, dtype=np.float64)
+    a = rng.normal(0.0, 1.0, size=n_modes)
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+
+    def f(x):
+        g = np.cos(2.0 * np.pi * (x @ kap.T) + ph) @ a
+        return lo + (hi - lo) * 0.5 * (1.0 + np.tanh(g))
+    return f
+
+
+def inverse_2d(n: int = 10, m: int = 2, jp: int = 6, n_receivers: int = 32, seed: int = 0) -> InverseSetup:
+    """d = 2 receiver-misfit setup: c^2 a seeded smooth field in [0.5, 2] on the
+    (2^jp+1)^2 nodes; source Gaussian (sigma 0.05, centre (0.3, 0.5)) x Ricker
+    (f_p 8); receivers (r + 1/2)/n_receivers, 0.9); observations from c^2 times
+    (1 + 0.2 exp(-|x - (0.6, 0.7)|^2 / 0.02)); misfit on target times of level n - m."""
+    base = Problem(d=2, lo=(0.0, 0.0), hi=(1.0, 1.0), T=1.0, c2=lambda x: np.ones(len(x)),
+                   name=f"inverse_2d_n{n}", **levels_nm(n, m))
+    x = param_nodes(2, jp)
+    c2 = smooth_field(2, seed)(x)
+    bump = 1.0 + 0.2 * np.exp(-np.sum((x - np.array([0.6, 0.7])) ** 2, axis=1) / 0.02)
+    rec = np.stack([(np.arange(n_receivers) + 0.5) / n_receivers, np.full(n_receivers, 0.9)], axis=1)
+    return InverseSetup(base=base, jp=jp, c2_nodal=c2, g_nodal=gaussian((0.3, 0.5))(x), s=ricker(8.0),
+                        receivers=rec, jt_star=n - m, c2_obs_nodal=c2 * bump)
