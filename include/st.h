@@ -143,6 +143,17 @@ st_status st_solve_component(st_handle* h, int k, st_solve_info* info);
  * Requires every component to be solved (ST_ERR_STATE otherwise). */
 st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev);
 
+/* The part of the sum of Eq. (19) contributed by the listed components
+ * comps[0..ncomp-1] (distinct indices, each solved), on the same target grid
+ * and layout as st_combine.  Eq. (19) is linear in the components, so the
+ * parts of disjoint sets that cover all components add up to st_combine's
+ * result: the combination step of a run that shards components over GPUs
+ * (each rank combines its own, then one sum-reduction of the target array).
+ * Handles with more than 64 components are refused (ST_ERR_ARG); so are
+ * repeated or out-of-range indices; an unsolved listed component gives
+ * ST_ERR_STATE.  Partial-sum buffers are cached per (target, set). */
+st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* comps, int ncomp, double* out_dev);
+
 /* Copy the FP64 coefficient array U_k (n_time x n_space, time-major) of a
  * solved component to caller-owned host memory. */
 st_status st_component_coeffs(st_handle* h, int k, double* host_out);

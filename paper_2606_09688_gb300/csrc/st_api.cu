@@ -24,6 +24,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -255,7 +256,7 @@ struct st_handle {
     std::vector<int> first;     // first[lev] = first component of level lev
     std::vector<double*> Y;     // partial sums of the levels below the target
   };
-  std::map<std::pair<int, int>, CombTables> comb;  // per target level pair
+  std::map<std::tuple<int, int, uint64_t>, CombTables> comb;  // per target level pair and component set
 
   // Optional per-kernel-class timing: CUDA events recorded on the handle's
   // stream around every launch, with the algorithmic bytes and flops of it.
@@ -1445,17 +1446,33 @@ st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
 
 st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
   if (!h || !out_dev) return ST_ERR_ARG;
+  std::vector<int> all(h->comps.size());
+  for (size_t k = 0; k < all.size(); ++k) all[k] = (int)k;
+  return st_combine_subset(h, jx_star, jt_star, all.data(), (int)all.size(), out_dev);
+}
+
+st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* comps, int ncomp, double* out_dev) {
+  if (!h || !out_dev || !comps || ncomp < 1) return ST_ERR_ARG;
   if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
-  for (auto& c : h->comps)
-    if (!c->solved) return fail(h, ST_ERR_STATE, "combine before every component is solved");
+  if (h->comps.size() > 64) return fail(h, ST_ERR_ARG, "more than 64 components");
+  uint64_t mask = 0;
+  for (int i = 0; i < ncomp; ++i) {
+    const int k = comps[i];
+    if (k < 0 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
+    if (mask & (1ull << k)) return fail(h, ST_ERR_ARG, "component listed twice");
+    mask |= 1ull << k;
+    if (!h->comps[k]->solved) return fail(h, ST_ERR_STATE, "combine before every listed component is solved");
+  }
   const st_problem& p = h->prob;
-  const int nc = (int)h->comps.size(), nts = (1 << jt_star) + 1;
-  auto key = std::make_pair(jx_star, jt_star);
+  const int nts = (1 << jt_star) + 1;
+  auto key = std::make_tuple(jx_star, jt_star, mask);
   if (!h->comb.count(key)) {
     // Components sorted by their combination level min(jx, jx*); B-spline tables
     // of every component at every target time; partial-sum buffers per level.
-    std::vector<int> order(nc);
-    for (int c = 0; c < nc; ++c) order[c] = c;
+    std::vector<int> order;
+    for (int c = 0; c < (int)h->comps.size(); ++c)
+      if (mask & (1ull << c)) order.push_back(c);
+    const int nc = (int)order.size();
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return std::min(h->comps[a]->jx, jx_star) < std::min(h->comps[b]->jx, jx_star);
     });

@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.st_component.argtypes = [C.c_void_p, C.c_int, C.POINTER(StComponentInfo)]
     lib.st_solve_component.argtypes = [C.c_void_p, C.c_int, C.POINTER(StSolveInfo)]
     lib.st_combine.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.st_combine_subset.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]
     lib.st_component_coeffs.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     lib.st_total_dofs.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     lib.st_kernel_launches.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
@@ -244,6 +245,20 @@ class Solver:
             out = torch.empty((nts, nsp), dtype=torch.float64, device="cuda")
         assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous() and out.numel() == nts * nsp
         self._check(self._lib.st_combine(self._h, jx_star, jt_star, C.c_void_p(out.data_ptr())))
+        return out
+
+    def combine_subset(self, jx_star: int, jt_star: int, comps, out=None):
+        """Contribution of the listed components to u^CF on the target grid
+        (st_combine_subset); disjoint sets covering all components sum to combine()."""
+        import torch
+        nsp = ((1 << jx_star) + 1) ** self.problem.d
+        nts = (1 << jt_star) + 1
+        if out is None:
+            out = torch.empty((nts, nsp), dtype=torch.float64, device="cuda")
+        assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous() and out.numel() == nts * nsp
+        ks = [int(k) for k in comps]
+        arr = (C.c_int * len(ks))(*ks)
+        self._check(self._lib.st_combine_subset(self._h, jx_star, jt_star, arr, len(ks), C.c_void_p(out.data_ptr())))
         return out
 
     def coeffs(self, k: int) -> np.ndarray:

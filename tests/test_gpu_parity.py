@@ -140,3 +140,28 @@ def test_errors_are_reported():
         with pytest.raises(StError) as e:
             s.solve(99)
         assert e.value.code == B.ST_ERR_ARG
+
+
+def test_combine_subset_parts_add_up_to_the_combination():
+    """Sharded combination (st_combine_subset): the parts of the ranks of an
+    LPT partition sum to st_combine's result and to the oracle's."""
+    from paper_2606_09688_gb300 import Solver, StError, shard
+    from paper_2606_09688_gb300 import st as B
+    p = W.layered_2d(8, 2)
+    target = (6, 6)
+    with Solver(p, precision=0) as s:
+        with pytest.raises(StError) as e:
+            s.combine_subset(*target, [0])
+        assert e.value.code == B.ST_ERR_STATE          # component 0 not solved yet
+        s.solve(-1)
+        full = s.combine(*target).cpu().numpy()
+        parts = shard.partition(shard.component_costs(s), 3)
+        acc = sum(s.combine_subset(*target, ks).cpu().numpy() for ks in parts if ks)
+        for bad in ([0, 0], [99], [-1]):
+            with pytest.raises(StError) as e:
+                s.combine_subset(*target, bad)
+            assert e.value.code == B.ST_ERR_ARG
+    assert np.max(np.abs(acc - full)) <= 1e-13 * np.max(np.abs(full))
+    comps, sols = osolve.solve_all(p, method="schur")
+    pts, times = osolve.target_grid(p, *target)
+    assert _rel(acc, osolve.combine(p, comps, sols, pts, times)) < TOL64
