@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="layered_2d_n12", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="layered_2d_n12", choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"],
                     help="precision of the headline value; the other one is reported beside it")
     ap.add_argument("--skip", default="", help="comma list of: other,profile,e2e,cpu")
@@ -446,10 +446,55 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batching configuration: 64 independent 2D instances (levels n in 8..12,
+    random smooth c^2 in [0.5, 2] with a jump, random Gaussian sources), all
+    components of all instances solved together by st_solve_batch.  Value =
+    space-time DOFs of all instances per second of the batch solve (combination
+    excluded: each instance's own target grid would total ~120 GB)."""
+    import torch
+    from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64, Solver, solve_batch
+    torch.cuda.set_device(0)
+    code = ST_FP64 if args.precision == "fp64" else ST_FP32_IR
+    probs = W.batch_instances(64)
+    t0 = time.perf_counter()
+    solvers = [Solver(p, precision=code, inner_tol=args.inner_tol, max_direct_rows=args.max_direct_rows)
+               for p in probs]
+    setup_s = time.perf_counter() - t0
+    dofs = sum(s.total_dofs for s in solvers)
+    for _ in range(args.warmup):
+        solve_batch(solvers)
+    torch.cuda.synchronize()
+    times = []
+    info = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        info = solve_batch(solvers)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    levels = {}
+    for p in probs:
+        levels[p.J + 2 * p.mx] = levels.get(p.J + 2 * p.mx, 0) + 1
+    line = {"metric": METRIC, "value": dofs / (ms / 1e3), "unit": "DOFs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if code == ST_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch64", "instances": len(probs), "levels_n": levels, "space_time_dofs": dofs,
+                       "timing": "host wall clock around st_solve_batch (blocking, all streams synchronised)",
+                       "combination": "excluded"},
+            "setup_s": setup_s, "sweeps": info.sweeps, "inner_iters": info.max_inner_iters,
+            "backward_error": info.backward_error}
+    for s in solvers:
+        s.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

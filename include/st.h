@@ -136,6 +136,15 @@ st_status st_component(const st_handle* h, int k, st_component_info* info);
  * synchronises and fills info (for k == -1, the worst component). */
 st_status st_solve_component(st_handle* h, int k, st_solve_info* info);
 
+/* Solve every component of n independent handles (instances) together: the
+ * (handle, component) pairs, largest first, are taken by a pool of at most
+ * max_threads host threads (0 = 32), each component on its own stream, so
+ * components of different instances overlap on the GPU.  Each handle's
+ * stream waits for its components.  info (nullable): the worst component
+ * over all handles; with info the call synchronises every handle's stream.
+ * A handle listed twice is refused (ST_ERR_ARG). */
+st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_info* info);
+
 /* Evaluate u^CF of Eq. (19) on the nodal target grid of spatial level jx_star
  * and temporal level jt_star: (2^jx*+1)^d nodes (boundary included,
  * lexicographic, x fastest) times 2^jt*+1 uniform times of [0,T] (time
@@ -153,6 +162,42 @@ st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev);
  * repeated or out-of-range indices; an unsolved listed component gives
  * ST_ERR_STATE.  Partial-sum buffers are cached per (target, set). */
 st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* comps, int ncomp, double* out_dev);
+
+/* ---------------------------------------------------------------------
+ * Receiver misfit and its gradient (adjoint of Eq. (9); an extension: the
+ * paper states the forward problem only).
+ *
+ * Receivers: x_rec (host, n_rec x d, inside the closed domain).  Target
+ * times: t_s = s T / 2^jt* (s = 0 .. 2^jt*).
+ *
+ * st_receiver_values: out_dev (device, (2^jt*+1) x n_rec, time slowest) =
+ * u^CF(x_r, t_s) of Eq. (19), evaluated from the components directly (the
+ * same values as st_combine's target grid interpolated multilinearly).
+ * Requires every component solved (ST_ERR_STATE).
+ *
+ * st_misfit_gradient: J = 1/2 sum_s w_s sum_r (u^CF(x_r, t_s) - d[s][r])^2
+ * with trapezoid weights w_s on [0, T] and observations d_obs_dev (device,
+ * same layout as out_dev above); its gradient with respect to
+ *   - c^2 given by nodal values on the uniform grid of level jp of the box
+ *     ((2^jp+1)^d nodes, x fastest) and sampled at cell centres by
+ *     multilinear interpolation, into dc2_dev (device, (2^jp+1)^d doubles);
+ *   - the spatial factor g of the first separable source term, given by
+ *     nodal values on the same grid and interpolated multilinearly to the
+ *     nodes of every component level, into dg_dev (zero if there is no
+ *     source term).
+ * For each component k it solves the adjoint system S_k^T L_k = G_k
+ * (G_k = coef_k E_k^T (w * misfit), E_k the evaluation at the receivers) with
+ * the forward machinery (transposed time factors, same spatial modes, the
+ * same precision and refinement as the handle), then reduces
+ * dJ/dc2_e = -L_k^T (B (x) K_e) U_k per cell and dJ/dg = M_load^T sum_i b[i] L_k[i]
+ * onto the parameter grid.  The caller promises that c^2 and g are the
+ * multilinear interpolants of nodal fields on that grid; the library cannot
+ * check it.  u0 must be zero (ST_ERR_ARG otherwise).  J_out is written on the
+ * host; info (nullable) reports the adjoint solves like st_solve_component.
+ * Synchronises the handle's stream before returning. */
+st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev);
+st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int n_rec, const double* d_obs_dev,
+                             int jp, double* J_out, double* dc2_dev, double* dg_dev, st_solve_info* info);
 
 /* Copy the FP64 coefficient array U_k (n_time x n_space, time-major) of a
  * solved component to caller-owned host memory. */

@@ -628,24 +628,6 @@ __global__ void __launch_bounds__(kBlock) k_residual_fused(Geo g, StencilCoef sc
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_time_combine(const double* __restrict__ Aband,
-                                                         const double* __restrict__ Bband,
-                                                         const double* __restrict__ F, const double* __restrict__ KU,
-                                                         const double* __restrict__ MU, double* __restrict__ Rout,
-                                                         int nt, int64_t nx) {
-  const int i = blockIdx.y;
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nx) return;
-  double acc = F[(int64_t)i * nx + a];
-#pragma unroll
-  for (int t = -2; t <= 2; ++t) {
-    const int j = i + t;
-    if (j < 0 || j >= nt) continue;
-    acc -= Aband[i * 5 + t + 2] * MU[(int64_t)j * nx + a] + Bband[i * 5 + t + 2] * KU[(int64_t)j * nx + a];
-  }
-  Rout[(int64_t)i * nx + a] = acc;
-}
-
 __global__ void __launch_bounds__(kBlock) k_norm2_partial(const double* __restrict__ v, int64_t n,
                                                           double* __restrict__ part) {
   double acc = 0.0;
@@ -911,6 +893,226 @@ template <typename R> __global__ void k_identity(cx<R>* __restrict__ I, int64_t 
   I[e] = mk<R>(r == j ? R(1) : R(0), R(0));
 }
 
+// ----------------------------------------------- receiver misfit gradient
+template <int D> __device__ __forceinline__ void param_weights(const ParamGrid& pg, const double x[3], int node[8],
+                                                               double w[8]) {
+  int c[3];
+  double f[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double t = (x[k] - pg.lo[k]) / pg.h[k];
+    int ci = (int)floor(t);
+    ci = ci < 0 ? 0 : (ci > pg.Np - 1 ? pg.Np - 1 : ci);
+    c[k] = ci;
+    f[k] = t - ci;
+  }
+#pragma unroll
+  for (int e = 0; e < (1 << D); ++e) {
+    double ww = 1.0;
+    int idx = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int b = (e >> k) & 1;
+      ww *= b ? f[k] : 1.0 - f[k];
+      idx += (c[k] + b) * st;
+      st *= pg.Np + 1;
+    }
+    node[e] = idx;
+    w[e] = ww;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_receiver_eval(const CombComp* __restrict__ comps, int ncomp,
+                                                          const RecCorner* __restrict__ rc, int nrec, int ncorner,
+                                                          const double* __restrict__ tbv,
+                                                          const int* __restrict__ tspan, int nts,
+                                                          double* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.y;
+  if (r >= nrec) return;
+  double val = 0.0;
+  for (int c = 0; c < ncomp; ++c) {
+    const CombComp cc = comps[c];
+    const int n = (1 << cc.jx) - 1, nt = (1 << cc.jt) + 1;
+    int64_t nx = n;  // interior nodes of the component grid (ncorner = 2^d)
+    for (int k = 2; k < ncorner; k <<= 1) nx *= n;
+    const int span = tspan[(int64_t)c * nts + s];
+    const double* tb = tbv + ((int64_t)c * nts + s) * 3;
+    double vc = 0.0;
+    for (int e = 0; e < ncorner; ++e) {
+      const RecCorner q = rc[((int64_t)c * nrec + r) * ncorner + e];
+      double u = 0.0;
+      if (q.interior >= 0)
+        for (int t = 0; t < 3; ++t) {
+          const int row = span + t - 1;
+          if (row >= 0 && row < nt) u = fma(tb[t], cc.U[(int64_t)row * nx + q.interior], u);
+        }
+      if (cc.lift != nullptr) u += cc.lift[q.all];
+      vc = fma(q.w, u, vc);
+    }
+    val = fma((double)cc.coef, vc, val);
+  }
+  out[(int64_t)s * nrec + r] = val;
+}
+
+__global__ void __launch_bounds__(kBlock) k_misfit(const double* __restrict__ vals, const double* __restrict__ dobs,
+                                                   int nts, int nrec, double T, double* __restrict__ wm,
+                                                   double* __restrict__ Jout) {
+  const double dt = T / (double)(nts - 1);
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < nts * nrec; e += blockDim.x) {
+    const int s = e / nrec;
+    const double w = (s == 0 || s == nts - 1) ? 0.5 * dt : dt;
+    const double m = vals[e] - dobs[e];
+    wm[e] = w * m;
+    acc = fma(w * m, m, acc);
+  }
+  const cx<double> t = block_sum(mk<double>(acc, 0.0));
+  if (threadIdx.x == 0) Jout[0] = 0.5 * t.re;
+}
+
+// ehat[i][r] = sum_s psi_i(t_s) wm[s][r] (one thread per receiver, no races)
+__global__ void k_adj_time_project(const double* __restrict__ wm, int nts, int nrec, const double* __restrict__ tb,
+                                   const int* __restrict__ tspan, int nt, double* __restrict__ ehat) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrec) return;
+  for (int i = 0; i < nt; ++i) ehat[(int64_t)i * nrec + r] = 0.0;
+  for (int s = 0; s < nts; ++s) {
+    const double m = wm[(int64_t)s * nrec + r];
+    for (int t = 0; t < 3; ++t) {
+      const int row = tspan[s] + t - 1;
+      if (row >= 0 && row < nt) ehat[(int64_t)row * nrec + r] = fma(tb[s * 3 + t], m, ehat[(int64_t)row * nrec + r]);
+    }
+  }
+}
+
+__global__ void k_adj_scatter(const double* __restrict__ ehat, int nrec, int nt, const RecCorner* __restrict__ rc,
+                              int ncorner, double coef, int64_t nx, double* __restrict__ G) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (r >= nrec || i >= nt) return;
+  const double v = coef * ehat[(int64_t)i * nrec + r];
+  for (int e = 0; e < ncorner; ++e) {
+    const RecCorner q = rc[(int64_t)r * ncorner + e];
+    if (q.interior >= 0) atomicAdd(&G[(int64_t)i * nx + q.interior], q.w * v);
+  }
+}
+
+// One thread per cell of the level: g_e = -sum_i L_i|_e^T K_ref Z_i|_e with
+// Z_i = sum_j B[i][j] U_j, then P^T onto the parameter nodes.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_grad_c2(Geo g, double lo0, double lo1, double lo2, double h0, double h1,
+                                                    double h2, int nt, const double* __restrict__ Bband,
+                                                    const double* __restrict__ U, const double* __restrict__ L,
+                                                    ElemK ke, ParamGrid pg, double* __restrict__ dc2) {
+  constexpr int NC = 1 << D;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.ncells) return;
+  int cidx[3] = {0, 0, 0};
+  {
+    int64_t r = e;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      cidx[k] = (int)(r % g.N);
+      r /= g.N;
+    }
+  }
+  int node[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    int idx = 0, st = 1;
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int p = cidx[k] + ((c >> k) & 1);  // all-node coordinate
+      in = in && p >= 1 && p <= g.N - 1;
+      idx += (p - 1) * st;
+      st *= g.n;
+    }
+    node[c] = in ? idx : -1;
+  }
+  const int64_t nx = g.nnodes;
+  double acc = 0.0;
+  for (int i = 0; i < nt; ++i) {
+    double Z[NC], Lv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double z = 0.0;
+      if (node[c] >= 0)
+        for (int t = -2; t <= 2; ++t) {
+          const int j = i + t;
+          if (j >= 0 && j < nt) z = fma(Bband[i * 5 + t + 2], U[(int64_t)j * nx + node[c]], z);
+        }
+      Z[c] = z;
+      Lv[c] = node[c] >= 0 ? L[(int64_t)i * nx + node[c]] : 0.0;
+    }
+#pragma unroll
+    for (int p = 0; p < NC; ++p) {
+      double kz = 0.0;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) kz = fma(ke.k[p * NC + q], Z[q], kz);
+      acc = fma(Lv[p], kz, acc);
+    }
+  }
+  const double x[3] = {lo0 + (cidx[0] + 0.5) * h0, lo1 + (cidx[1] + 0.5) * h1, lo2 + (cidx[2] + 0.5) * h2};
+  int pn[8];
+  double pw[8];
+  param_weights<D>(pg, x, pn, pw);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) atomicAdd(&dc2[pn[c]], -acc * pw[c]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_grad_g_v(int nt, int64_t nx, const double* __restrict__ b,
+                                                     const double* __restrict__ L, double* __restrict__ v) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nx) return;
+  double acc = 0.0;
+  for (int i = 0; i < nt; ++i) acc = fma(b[i], L[(int64_t)i * nx + a], acc);
+  v[a] = acc;
+}
+
+// One thread per node of the level (boundary included): (M_load^T v)(m) =
+// sum over interior neighbours a of mtot[a - m] v[a], then Q^T onto the parameter nodes.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_grad_g(Geo g, double lo0, double lo1, double lo2, double h0, double h1,
+                                                   double h2, StencilCoef sc, const double* __restrict__ v,
+                                                   ParamGrid pg, double* __restrict__ dg) {
+  constexpr int NS = ipow3(D);
+  int64_t nall = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) nall *= (g.N + 1);
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nall) return;
+  int P[3] = {0, 0, 0};
+  {
+    int64_t r = m;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      P[k] = (int)(r % (g.N + 1));
+      r /= (g.N + 1);
+    }
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int ss = s, idx = 0, st = 1;
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int q = P[k] + ss % 3 - 1;
+      ss /= 3;
+      in = in && q >= 1 && q <= g.N - 1;
+      idx += (q - 1) * st;
+      st *= g.n;
+    }
+    if (in) acc = fma(sc.mtot[s], v[idx], acc);
+  }
+  const double x[3] = {lo0 + P[0] * h0, lo1 + P[1] * h1, lo2 + P[2] * h2};
+  int pn[8];
+  double pw[8];
+  param_weights<D>(pg, x, pn, pw);
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) atomicAdd(&dg[pn[c]], acc * pw[c]);
+}
+
 }  // namespace
 
 // ================================================================ wrappers
@@ -1073,6 +1275,50 @@ void launch_dense_coarse(const cx<R>* Ainv, int64_t n, const cx<R>* b, cx<R>* x,
 template <typename R> void launch_identity(cx<R>* I, int64_t n, cudaStream_t s) {
   count(1);
   k_identity<R><<<blocks_for(n * n), kBlock, 0, s>>>(I, n);
+}
+
+void launch_receiver_eval(const CombComp* comps, int ncomp, const RecCorner* rc, int nrec, int ncorner,
+                          const double* tbv, const int* tspan, int nts, double* out, cudaStream_t s) {
+  count(1);
+  k_receiver_eval<<<dim3((nrec + kBlock - 1) / kBlock, nts), kBlock, 0, s>>>(comps, ncomp, rc, nrec, ncorner, tbv,
+                                                                             tspan, nts, out);
+}
+
+void launch_misfit(const double* vals, const double* dobs, int nts, int nrec, double T, double* wm, double* Jout,
+                   cudaStream_t s) {
+  count(1);
+  k_misfit<<<1, kBlock, 0, s>>>(vals, dobs, nts, nrec, T, wm, Jout);
+}
+
+void launch_adjoint_rhs(const double* wm, int nts, int nrec, const double* tb, const int* tspan, int nt,
+                        const RecCorner* rc, int ncorner, double coef, int64_t nx, double* ehat, double* G,
+                        cudaStream_t s) {
+  count(2);
+  k_adj_time_project<<<(nrec + 63) / 64, 64, 0, s>>>(wm, nts, nrec, tb, tspan, nt, ehat);
+  k_adj_scatter<<<dim3((nrec + 63) / 64, nt), 64, 0, s>>>(ehat, nrec, nt, rc, ncorner, coef, nx, G);
+}
+
+void launch_grad_c2(const Geo& g, const double* lo, int nt, const double* Bband, const double* U, const double* L,
+                    const ElemK& ke, const ParamGrid& pg, double* dc2, cudaStream_t s) {
+  count(1);
+  const double h0 = pg.h[0] * pg.Np / g.N, h1 = pg.h[1] * pg.Np / g.N, h2 = pg.h[2] * pg.Np / g.N;
+  const unsigned grid = blocks_for(g.ncells);
+  if (g.d == 1) k_grad_c2<1><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, nt, Bband, U, L, ke, pg, dc2);
+  else if (g.d == 2) k_grad_c2<2><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, nt, Bband, U, L, ke, pg, dc2);
+  else k_grad_c2<3><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, nt, Bband, U, L, ke, pg, dc2);
+}
+
+void launch_grad_g(const Geo& g, const double* lo, const StencilCoef& sc, int nt, const double* b, const double* L,
+                   double* v, const ParamGrid& pg, double* dg, cudaStream_t s) {
+  count(2);
+  k_grad_g_v<<<blocks_for(g.nnodes), kBlock, 0, s>>>(nt, g.nnodes, b, L, v);
+  const double h0 = pg.h[0] * pg.Np / g.N, h1 = pg.h[1] * pg.Np / g.N, h2 = pg.h[2] * pg.Np / g.N;
+  int64_t nall = 1;
+  for (int k = 0; k < g.d; ++k) nall *= (g.N + 1);
+  const unsigned grid = blocks_for(nall);
+  if (g.d == 1) k_grad_g<1><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, sc, v, pg, dg);
+  else if (g.d == 2) k_grad_g<2><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, sc, v, pg, dg);
+  else k_grad_g<3><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, sc, v, pg, dg);
 }
 
 int64_t kernel_launch_count() { return g_launches.load(); }

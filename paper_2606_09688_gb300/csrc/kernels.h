@@ -101,6 +101,41 @@ void launch_dense_coarse(const cx<R>* Ainv, int64_t n, const cx<R>* b, cx<R>* x,
 // I (n x n identity, column j at j * n): right-hand sides of the inversion.
 template <typename R> void launch_identity(cx<R>* I, int64_t n, cudaStream_t s);
 
+// ------------------------------------------------ receiver misfit gradient
+// Corner of the cell holding a receiver at one component's level: interior
+// node index (-1 on the boundary), all-node index, multilinear weight.
+struct RecCorner {
+  int interior;
+  int all;
+  double w;
+};
+// Uniform grid of nodal parameters on the domain box: Np cells per direction.
+struct ParamGrid {
+  int d, Np;
+  double lo[3], h[3];
+};
+// Element stiffness of one cell with c^2 = 1 (2^d x 2^d, local corner c has
+// bit k set at the upper end in direction k).
+struct ElemK {
+  double k[64];
+};
+// out[s][r] = sum_c coef_c u_c(x_r, t_s) for all target times s (nts) and receivers r.
+void launch_receiver_eval(const CombComp* comps, int ncomp, const RecCorner* rc, int nrec, int ncorner,
+                          const double* tbv, const int* tspan, int nts, double* out, cudaStream_t s);
+// wm[s][r] = w_s (vals - dobs)[s][r] with trapezoid weights on [0, T]; J = 1/2 sum w_s e^2 -> Jout[0].
+void launch_misfit(const double* vals, const double* dobs, int nts, int nrec, double T, double* wm, double* Jout,
+                   cudaStream_t s);
+// G (nt x nx) += coef sum_s sum_r psi_i(t_s) phi_a(x_r) wm[s][r] for one component (G zeroed by the caller).
+void launch_adjoint_rhs(const double* wm, int nts, int nrec, const double* tb, const int* tspan, int nt,
+                        const RecCorner* rc, int ncorner, double coef, int64_t nx, double* ehat, double* G,
+                        cudaStream_t s);
+// dc2 (param nodes) += P^T g with g_e = -sum_ij B[i][j] L_i^T K_e U_j per cell e of the level.
+void launch_grad_c2(const Geo& g, const double* lo, int nt, const double* Bband, const double* U, const double* L,
+                    const ElemK& ke, const ParamGrid& pg, double* dc2, cudaStream_t s);
+// dg (param nodes) += Q^T M_load^T sum_i b[i] L_i (v: scratch of nx doubles).
+void launch_grad_g(const Geo& g, const double* lo, const StencilCoef& sc, int nt, const double* b, const double* L,
+                   double* v, const ParamGrid& pg, double* dg, cudaStream_t s);
+
 // Kernels launched by this process through the wrappers above.
 int64_t kernel_launch_count();
 void note_launches(int k);

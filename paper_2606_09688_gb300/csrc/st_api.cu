@@ -15,6 +15,7 @@
 // U = C Phi^T.
 // Both are wrapped in FP64 iterative refinement on R = F - (A (x) M + B (x) K) U.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -143,8 +144,12 @@ struct TimeData {
   bool have_eig = false;
   double* Aband = nullptr;  // nt x 5
   double* Bband = nullptr;
+  double* ATband = nullptr;  // transposes (adjoint systems)
+  double* BTband = nullptr;
   cx<double>* W = nullptr;  // nsel x nt
   cx<double>* V = nullptr;  // nt x nsel
+  cx<double>* VT = nullptr;  // nsel x nt: forward transform of the adjoint systems
+  cx<double>* WT = nullptr;  // nt x nsel: their back transform
   double* wq = nullptr;
   cx<double>* lam64 = nullptr;
   cx<float>* lam32 = nullptr;
@@ -205,7 +210,13 @@ struct Component {
   double* PhiT = nullptr;
   double* ab = nullptr;
   int* piv = nullptr;
+  double* abT = nullptr;  // LU of (A + mu B)^T per spatial mode (adjoint systems)
+  int* pivT = nullptr;
   int kl = 2, ku = 2;
+  // adjoint state (receiver misfit gradient): right-hand side and solution, n_t x n_x
+  double* Gadj = nullptr;
+  double* Lam = nullptr;
+  bool adj_solved = false;
   double Snorm = 0.0;  // upper bound of ||A (x) M + B (x) K||_2
   st_solve_info info{};
   int nactive = 0;  // modes still iterating at the last host check (for byte accounting)
@@ -257,6 +268,21 @@ struct st_handle {
     std::vector<double*> Y;     // partial sums of the levels below the target
   };
   std::map<std::tuple<int, int, uint64_t>, CombTables> comb;  // per target level pair and component set
+
+  // Receiver tables of the misfit gradient (one receiver set cached).
+  struct RecTables {
+    int jt = -1, nrec = 0, ncorner = 0, nts = 0;
+    std::vector<double> x;        // receiver coordinates (nrec x d)
+    CombComp* comps = nullptr;    // components in component order
+    RecCorner* rc = nullptr;      // ncomp x nrec x 2^d
+    double* tb = nullptr;         // ncomp x nts x 3 B-spline values at the target times
+    int* span = nullptr;          // ncomp x nts
+    double* vals = nullptr;       // nts x nrec
+    double* wm = nullptr;         // weighted misfit, nts x nrec
+    double* J = nullptr;          // 1
+    double* ehat = nullptr;       // max nt x nrec
+    double* gv = nullptr;         // max nx
+  } rec;
 
   // Optional per-kernel-class timing: CUDA events recorded on the handle's
   // stream around every launch, with the algorithmic bytes and flops of it.
@@ -574,6 +600,19 @@ st_status setup_time_level(st_handle* h, int jt, TimeData& td) {
   td.Bband = h->upload(Bb);
   ST_NEED(h, td.Aband);
   ST_NEED(h, td.Bband);
+  // transposed bands: row i holds A(j, i) for j = i - 2 .. i + 2
+  std::vector<double> ATb((size_t)nt * 5, 0.0), BTb((size_t)nt * 5, 0.0);
+  for (int i = 0; i < nt; ++i)
+    for (int t = -2; t <= 2; ++t) {
+      const int j = i + t;
+      if (j < 0 || j >= nt) continue;
+      ATb[(size_t)i * 5 + t + 2] = td.tl.A[(size_t)j * nt + i];
+      BTb[(size_t)i * 5 + t + 2] = td.tl.B[(size_t)j * nt + i];
+    }
+  td.ATband = h->upload(ATb);
+  td.BTband = h->upload(BTb);
+  ST_NEED(h, td.ATband);
+  ST_NEED(h, td.BTband);
   // RHS time coefficient rows: (s_r, psi_i')_e, psi_i'(0), -(1, psi_i')_e.
   const int nrows = h->nterm_rows;
   std::vector<double> coef((size_t)nrows * nt, 0.0);
@@ -717,24 +756,30 @@ st_status setup_component(st_handle* h, Component& c) {
     ST_NEED(h, c.Phi);
     ST_NEED(h, c.PhiT);
     const int nt = c.nt, kl = 2, ku = 2, ld = 2 * kl + ku + 1;
-    std::vector<double> abAll((size_t)ld * nt * nx, 0.0);
-    std::vector<int> pivAll((size_t)nt * nx, 0);
-    std::vector<double> ab((size_t)ld * nt);
-    std::vector<int> piv;
-    for (int a = 0; a < nx; ++a) {
-      std::fill(ab.begin(), ab.end(), 0.0);
-      for (int j = 0; j < nt; ++j)
-        for (int i = std::max(0, j - ku); i <= std::min(nt - 1, j + kl); ++i)
-          ab[(size_t)(kl + ku + i - j) + (size_t)j * ld] =
-              c.td->tl.A[(size_t)i * nt + j] + mu[a] * c.td->tl.B[(size_t)i * nt + j];
-      if (!band_lu(nt, kl, ku, ab, piv)) return fail(h, ST_ERR_NUMERIC, "time band LU failed");
-      for (size_t e = 0; e < ab.size(); ++e) abAll[e * nx + a] = ab[e];
-      for (int j = 0; j < nt; ++j) pivAll[(size_t)j * nx + a] = piv[j];
+    // LU of A + mu_a B (forward) and of its transpose (adjoint) per spatial mode
+    for (int tr = 0; tr < 2; ++tr) {
+      std::vector<double> abAll((size_t)ld * nt * nx, 0.0);
+      std::vector<int> pivAll((size_t)nt * nx, 0);
+      std::vector<double> ab((size_t)ld * nt);
+      std::vector<int> piv;
+      for (int a = 0; a < nx; ++a) {
+        std::fill(ab.begin(), ab.end(), 0.0);
+        for (int j = 0; j < nt; ++j)
+          for (int i = std::max(0, j - ku); i <= std::min(nt - 1, j + kl); ++i) {
+            const size_t e = tr == 0 ? (size_t)i * nt + j : (size_t)j * nt + i;
+            ab[(size_t)(kl + ku + i - j) + (size_t)j * ld] = c.td->tl.A[e] + mu[a] * c.td->tl.B[e];
+          }
+        if (!band_lu(nt, kl, ku, ab, piv)) return fail(h, ST_ERR_NUMERIC, "time band LU failed");
+        for (size_t e = 0; e < ab.size(); ++e) abAll[e * nx + a] = ab[e];
+        for (int j = 0; j < nt; ++j) pivAll[(size_t)j * nx + a] = piv[j];
+      }
+      double* abd = h->upload(abAll);
+      int* pivd = h->upload(pivAll);
+      ST_NEED(h, abd);
+      ST_NEED(h, pivd);
+      (tr == 0 ? c.ab : c.abT) = abd;
+      (tr == 0 ? c.piv : c.pivT) = pivd;
     }
-    c.ab = h->upload(abAll);
-    c.piv = h->upload(pivAll);
-    ST_NEED(h, c.ab);
-    ST_NEED(h, c.piv);
     c.kl = kl;
     c.ku = ku;
     ST_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1094,36 +1139,57 @@ st_status read_norm(st_handle* h, Component& c, const double* v, int64_t n, doub
   return ccheck(c, "norm");
 }
 
-template <typename R> st_status sweep_time_eig(st_handle* h, Component& c, const double* Rin, int& iters) {
+// The operators of one component solve: the forward system S U = F, or the
+// adjoint system S^T L = G (transposed time factors; same spatial modes).
+struct SolveIO {
+  const double* rhs;
+  double* sol;
+  const cx<double>* Wf;  // forward transform (nsel x nt)
+  const cx<double>* Vb;  // back transform (nt x nsel)
+  const double* Ab;      // time bands of the residual
+  const double* Bb;
+  const double* lu_ab;   // space eigenbasis: band LU per spatial mode
+  const int* lu_piv;
+};
+
+SolveIO forward_io(Component& c) {
+  return SolveIO{c.F, c.U, c.td->W, c.td->V, c.td->Aband, c.td->Bband, c.ab, c.piv};
+}
+SolveIO adjoint_io(Component& c) {
+  return SolveIO{c.Gadj, c.Lam, c.td->VT, c.td->WT, c.td->ATband, c.td->BTband, c.abT, c.pivT};
+}
+
+template <typename R>
+st_status sweep_time_eig(st_handle* h, Component& c, const SolveIO& io, const double* Rin, int& iters) {
   Work<R>& w = work_of<R>(c);
   const double cs = sizeof(cx<R>), nx = (double)c.nx;
   PROF(h, c.cs, KC_TRANSFORM, (int64_t)(c.nx), c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
-       launch_fwd_transform<R>(c.td->W, Rin, w.G, c.nsel, c.nt, c.nx, c.cs));
+       launch_fwd_transform<R>(io.Wf, Rin, w.G, c.nsel, c.nt, c.nx, c.cs));
   st_status s = inner_solve<R>(h, c, iters);
   if (s != ST_OK) return s;
   PROF(h, c.cs, KC_TRANSFORM, (int64_t)(c.nx), 2.0 * c.nt * nx * 8.0 + c.nsel * nx * cs, 4.0 * c.nsel * c.nt * nx,
-       launch_back_transform<R>(c.td->V, c.td->wq, w.X, c.U, c.nsel, c.nt, c.nx, c.cs));
+       launch_back_transform<R>(io.Vb, c.td->wq, w.X, io.sol, c.nsel, c.nt, c.nx, c.cs));
   return ccheck(c, "time transforms");
 }
 
-st_status sweep_space_eig(st_handle* h, Component& c, const double* Rin) {
+st_status sweep_space_eig(st_handle* h, Component& c, const SolveIO& io, const double* Rin) {
   const double nx = (double)c.nx, nt = c.nt;
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
        launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, c.cs));
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
-       launch_time_band_solve(c.ab, c.piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
+       launch_time_band_solve(io.lu_ab, io.lu_piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
-       launch_gemm_right(c.KU, c.PhiT, c.U, c.nt, c.nx, 1, 1, c.cs));
+       launch_gemm_right(c.KU, c.PhiT, io.sol, c.nt, c.nx, 1, 1, c.cs));
   return ccheck(c, "space eigenbasis sweep");
 }
 
-st_status solve_one(st_handle* h, Component& c) {
-  st_status s = assemble_rhs(h, c);
-  if (s != ST_OK) return s;
+st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint) {
+  st_status s = ST_OK;
+  if (!adjoint && (s = assemble_rhs(h, c)) != ST_OK) return s;
   const size_t n = (size_t)c.nx * c.nt;
-  ST_CUDAC(c, cudaMemsetAsync(c.U, 0, n * sizeof(double), c.cs));
+  ST_CUDAC(c, cudaMemsetAsync(io.sol, 0, n * sizeof(double), c.cs));
   double fn = 0.0;
-  if ((s = read_norm(h, c, c.F, (int64_t)n, fn)) != ST_OK) return s;
+  if ((s = read_norm(h, c, io.rhs, (int64_t)n, fn)) != ST_OK) return s;
   // Refinement stops on the normwise backward error eta = ||R|| / (||S|| ||U|| + ||F||)
   // (the relative residual of an exact solution can be far above rounding
   // when S is ill-conditioned), or when a sweep no longer halves eta.
@@ -1131,20 +1197,21 @@ st_status solve_one(st_handle* h, Component& c) {
   const int max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 8;
   c.info = st_solve_info{};
   c.info.status = ST_OK;
+  bool& done = adjoint ? c.adj_solved : c.solved;
   if (fn == 0.0) {
-    c.solved = true;
+    done = true;
     return ST_OK;
   }
   double rel = 1.0, eta = 1.0, eta_prev = 1e300;
-  const double* Rin = c.F;
+  const double* Rin = io.rhs;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int iters = 0;
     if (c.method == 1) {
-      s = sweep_space_eig(h, c, Rin);
+      s = sweep_space_eig(h, c, io, Rin);
     } else if (c.inner64) {
-      s = sweep_time_eig<double>(h, c, Rin, iters);
+      s = sweep_time_eig<double>(h, c, io, Rin, iters);
     } else {
-      s = sweep_time_eig<float>(h, c, Rin, iters);
+      s = sweep_time_eig<float>(h, c, io, Rin, iters);
     }
     if (s != ST_OK) {
       c.info.status = s;
@@ -1154,11 +1221,11 @@ st_status solve_one(st_handle* h, Component& c) {
     c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
     PROF(h, c.cs, KC_RESIDUAL64, (int64_t)(c.nx), 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
          (double)n * (4.0 * ipow3(c.sl->geo.d) + 20.0),
-         launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, c.U, c.F, c.td->Aband, c.td->Bband, c.KU, c.MU, c.Rv, c.nt,
+         launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, io.sol, io.rhs, io.Ab, io.Bb, c.KU, c.MU, c.Rv, c.nt,
                          c.cs));
     double rn = 0.0, un = 0.0;
     if ((s = read_norm(h, c, c.Rv, (int64_t)n, rn)) != ST_OK) return s;
-    if ((s = read_norm(h, c, c.U, (int64_t)n, un)) != ST_OK) return s;
+    if ((s = read_norm(h, c, io.sol, (int64_t)n, un)) != ST_OK) return s;
     rel = rn / fn;
     eta = rn / (c.Snorm * un + fn);
     if (!std::isfinite(rel)) {
@@ -1171,7 +1238,7 @@ st_status solve_one(st_handle* h, Component& c) {
   }
   c.info.rel_residual = rel;
   c.info.backward_error = eta;
-  c.solved = true;
+  done = true;
   if (eta > 1e3 * tol && eta > 1e-12) {
     c.info.status = ST_ERR_NOT_CONVERGED;
     return cfail(c, ST_ERR_NOT_CONVERGED, "refinement did not reach the backward-error target");
@@ -1201,6 +1268,158 @@ st_status setup_context(st_handle* h, Component& c) {
     }
   }
   return ST_OK;
+}
+
+// Receiver tables: per component, the cell of each receiver at the
+// component's level (corner indices and multilinear weights) and the
+// component's B-spline values at the target times.  Rebuilt only when the
+// receivers or the target time level change.
+st_status build_receivers(st_handle* h, int jt_star, const double* x, int nrec) {
+  const st_problem& p = h->prob;
+  const int d = p.d, nc = 1 << d, ncomp = (int)h->comps.size(), nts = (1 << jt_star) + 1;
+  st_handle::RecTables& R = h->rec;
+  std::vector<double> xv(x, x + (size_t)nrec * d);
+  if (R.jt == jt_star && R.nrec == nrec && R.x == xv) return ST_OK;
+  for (int r = 0; r < nrec; ++r)
+    for (int k = 0; k < d; ++k) {
+      const double v = xv[(size_t)r * d + k];
+      if (!(v >= p.lo[k] && v <= p.hi[k])) return fail(h, ST_ERR_ARG, "receiver outside the domain");
+    }
+  std::vector<CombComp> cc(ncomp);
+  std::vector<RecCorner> rc((size_t)ncomp * nrec * nc);
+  std::vector<double> tb((size_t)ncomp * nts * 3);
+  std::vector<int> sp((size_t)ncomp * nts);
+  int64_t max_nx = 1;
+  int max_nt = 1;
+  for (int c = 0; c < ncomp; ++c) {
+    const Component& k = *h->comps[c];
+    cc[c] = CombComp{k.U, k.sl->lift, k.jx, k.jt, k.coef, 0};
+    max_nx = std::max(max_nx, k.nx);
+    max_nt = std::max(max_nt, k.nt);
+    const int N = 1 << k.jx, n = N - 1;
+    for (int r = 0; r < nrec; ++r) {
+      int cell[3] = {0, 0, 0};
+      double f[3] = {0, 0, 0};
+      for (int q = 0; q < d; ++q) {
+        const double t = (xv[(size_t)r * d + q] - p.lo[q]) / ((p.hi[q] - p.lo[q]) / N);
+        cell[q] = std::min(std::max((int)std::floor(t), 0), N - 1);
+        f[q] = t - cell[q];
+      }
+      for (int e = 0; e < nc; ++e) {
+        double w = 1.0;
+        int64_t all = 0, in = 0, sa = 1, si = 1;
+        bool interior = true;
+        for (int q = 0; q < d; ++q) {
+          const int b = (e >> q) & 1, P = cell[q] + b;
+          w *= b ? f[q] : 1.0 - f[q];
+          all += (int64_t)P * sa;
+          sa *= (N + 1);
+          interior = interior && P >= 1 && P <= n;
+          in += (int64_t)(P - 1) * si;
+          si *= n;
+        }
+        rc[((size_t)c * nrec + r) * nc + e] = RecCorner{interior ? (int)in : -1, (int)all, w};
+      }
+    }
+    const int Nt = 1 << k.jt;
+    for (int s = 0; s < nts; ++s) {
+      int span = (k.jt >= jt_star) ? (s << (k.jt - jt_star)) : (s >> (jt_star - k.jt));
+      span = std::min(span, Nt - 1);
+      double v[3], d1[3], d2[3];
+      bspline_local(Nt, p.T, span, p.T * (double)s / (double)(1 << jt_star), v, d1, d2);
+      for (int a = 0; a < 3; ++a) tb[((size_t)c * nts + s) * 3 + a] = v[a];
+      sp[(size_t)c * nts + s] = span;
+    }
+  }
+  R.comps = h->upload(cc);
+  R.rc = h->upload(rc);
+  R.tb = h->upload(tb);
+  R.span = h->upload(sp);
+  R.vals = h->alloc<double>((size_t)nts * nrec);
+  R.wm = h->alloc<double>((size_t)nts * nrec);
+  R.J = h->alloc<double>(1);
+  R.ehat = h->alloc<double>((size_t)max_nt * nrec);
+  R.gv = h->alloc<double>((size_t)max_nx);
+  if (!R.comps || !R.rc || !R.tb || !R.span || !R.vals || !R.wm || !R.J || !R.ehat || !R.gv)
+    return fail(h, ST_ERR_OOM, "device allocation failed");
+  R.jt = jt_star;
+  R.nrec = nrec;
+  R.ncorner = nc;
+  R.nts = nts;
+  R.x = xv;
+  return ST_OK;
+}
+
+// Q1 element stiffness with unit coefficient on a cell of widths h (local
+// corner c: bit k set at the upper end in direction k): the sum over
+// directions of the 1D stiffness in that direction times the 1D masses in the others.
+ElemK element_stiffness(int d, const double* h) {
+  ElemK ke{};
+  const int nc = 1 << d;
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b < nc; ++b) {
+      double sum = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double term = 1.0;
+        for (int l = 0; l < d; ++l) {
+          const int ba = (a >> l) & 1, bb = (b >> l) & 1;
+          term *= (l == k) ? (ba == bb ? 1.0 : -1.0) / h[l] : h[l] / 6.0 * (ba == bb ? 2.0 : 1.0);
+        }
+        sum += term;
+      }
+      ke.k[a * nc + b] = sum;
+    }
+  return ke;
+}
+
+// Forward (S U = F) or adjoint (S^T L = G) solves of components k0..k1-1.
+// Component streams start after the work already queued on the handle's
+// stream; independent components run concurrently, one host thread and one
+// stream each (one after the other with profiling on, so that event times are
+// not shared between overlapping kernels); the handle's stream then waits for
+// all of them.
+st_status run_solves(st_handle* h, int k0, int k1, bool adjoint, st_solve_info* info) {
+  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+  std::vector<st_status> st(k1 - k0, ST_OK);
+  for (int i = k0; i < k1; ++i) {
+    Component& c = *h->comps[i];
+    c.err.clear();
+    ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
+  }
+  auto run = [&](int i) {
+    Component& c = *h->comps[i];
+    st[i - k0] = solve_one(h, c, adjoint ? adjoint_io(c) : forward_io(c), adjoint);
+  };
+  if (k1 - k0 > 1 && !h->prof_on) {
+    std::vector<std::thread> pool;
+    pool.reserve(k1 - k0);
+    for (int i = k0; i < k1; ++i) pool.emplace_back(run, i);
+    for (auto& t : pool) t.join();
+  } else {
+    for (int i = k0; i < k1; ++i) run(i);
+  }
+  st_status worst = ST_OK;
+  st_solve_info agg{};
+  for (int i = k0; i < k1; ++i) {
+    Component& c = *h->comps[i];
+    ST_CUDA(h, cudaEventRecord(c.done, c.cs));
+    ST_CUDA(h, cudaStreamWaitEvent(h->stream, c.done, 0));
+    const st_solve_info& ci = c.info;
+    agg.sweeps = std::max(agg.sweeps, ci.sweeps);
+    agg.max_inner_iters = std::max(agg.max_inner_iters, ci.max_inner_iters);
+    agg.rel_residual = std::max(agg.rel_residual, ci.rel_residual);
+    agg.backward_error = std::max(agg.backward_error, ci.backward_error);
+    if (st[i - k0] != ST_OK && worst == ST_OK) {
+      worst = st[i - k0];
+      h->err = "component " + std::to_string(i) + ": " + c.err;
+    }
+  }
+  agg.status = worst;
+  if (info) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+    *info = agg;
+  }
+  return worst;
 }
 
 // Host-side phase times of st_setup, printed to stderr when the environment
@@ -1325,6 +1544,20 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
       }
       td.W = hp->upload(Wc);
       td.V = hp->upload(Vc);
+      // (B^-1 A)^T-side pencil of the adjoint: A^T = V^-T Lam V^T B^T, so its
+      // modes are reached by V^T and left by W^T = B^-T V^-T
+      std::vector<cx<double>> VTc((size_t)ns * ntt), WTc((size_t)ntt * ns);
+      for (int q = 0; q < ns; ++q)
+        for (int j = 0; j < ntt; ++j) {
+          VTc[(size_t)q * ntt + j] = Vc[(size_t)j * ns + q];
+          WTc[(size_t)j * ns + q] = Wc[(size_t)q * ntt + j];
+        }
+      td.VT = hp->upload(VTc);
+      td.WT = hp->upload(WTc);
+      if (!td.VT || !td.WT) {
+        g_create_error = "device allocation failed";
+        return ST_ERR_OOM;
+      }
       td.lam64 = hp->upload(lc);
       td.lam32 = hp->upload(lf);
       td.wq = hp->upload(td.eig.weight);
@@ -1400,45 +1633,69 @@ st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
   if (!h) return ST_ERR_ARG;
   if (k < -1 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
   const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? (int)h->comps.size() : k + 1;
-  // Component streams start after the work already queued on the handle's stream.
-  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
-  std::vector<st_status> st(k1 - k0, ST_OK);
-  for (int i = k0; i < k1; ++i) {
-    Component& c = *h->comps[i];
-    c.err.clear();
-    ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
+  return run_solves(h, k0, k1, false, info);
+}
+
+st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_info* info) {
+  if (!hs || n < 1 || max_threads < 0) return ST_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return ST_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(hs[i], ST_ERR_ARG, "a handle is listed twice");
   }
-  auto run = [&](int i) { st[i - k0] = solve_one(h, *h->comps[i]); };
-  // Independent components run concurrently, one host thread and one stream
-  // each; with profiling on they run one after the other so that event times
-  // are not shared between overlapping kernels.
-  if (k1 - k0 > 1 && !h->prof_on) {
+  // every (handle, component) pair, largest first, over a bounded pool of host threads
+  struct Task {
+    st_handle* h;
+    int k;
+    int64_t cost;
+  };
+  std::vector<Task> tasks;
+  for (int i = 0; i < n; ++i) {
+    st_handle* h = hs[i];
+    ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+    for (int k = 0; k < (int)h->comps.size(); ++k) {
+      Component& c = *h->comps[k];
+      c.err.clear();
+      ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
+      tasks.push_back(Task{h, k, c.nx * c.nt});
+    }
+  }
+  std::stable_sort(tasks.begin(), tasks.end(), [](const Task& a, const Task& b) { return a.cost > b.cost; });
+  std::vector<st_status> st(tasks.size(), ST_OK);
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t t = next.fetch_add(1); t < tasks.size(); t = next.fetch_add(1)) {
+      Component& c = *tasks[t].h->comps[tasks[t].k];
+      st[t] = solve_one(tasks[t].h, c, forward_io(c), false);
+    }
+  };
+  const int nth = (int)std::min<size_t>(tasks.size(), max_threads > 0 ? (size_t)max_threads : (size_t)32);
+  {
     std::vector<std::thread> pool;
-    pool.reserve(k1 - k0);
-    for (int i = k0; i < k1; ++i) pool.emplace_back(run, i);
-    for (auto& t : pool) t.join();
-  } else {
-    for (int i = k0; i < k1; ++i) run(i);
+    for (int i = 0; i < nth; ++i) pool.emplace_back(worker);
+    for (auto& th : pool) th.join();
   }
   st_status worst = ST_OK;
   st_solve_info agg{};
-  for (int i = k0; i < k1; ++i) {
-    Component& c = *h->comps[i];
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    st_handle* h = tasks[t].h;
+    Component& c = *h->comps[tasks[t].k];
     ST_CUDA(h, cudaEventRecord(c.done, c.cs));
     ST_CUDA(h, cudaStreamWaitEvent(h->stream, c.done, 0));
-    const st_solve_info& ci = c.info;
-    agg.sweeps = std::max(agg.sweeps, ci.sweeps);
-    agg.max_inner_iters = std::max(agg.max_inner_iters, ci.max_inner_iters);
-    agg.rel_residual = std::max(agg.rel_residual, ci.rel_residual);
-    agg.backward_error = std::max(agg.backward_error, ci.backward_error);
-    if (st[i - k0] != ST_OK && worst == ST_OK) {
-      worst = st[i - k0];
-      h->err = "component " + std::to_string(i) + ": " + c.err;
+    agg.sweeps = std::max(agg.sweeps, c.info.sweeps);
+    agg.max_inner_iters = std::max(agg.max_inner_iters, c.info.max_inner_iters);
+    agg.rel_residual = std::max(agg.rel_residual, c.info.rel_residual);
+    agg.backward_error = std::max(agg.backward_error, c.info.backward_error);
+    if (st[t] != ST_OK && worst == ST_OK) {
+      worst = st[t];
+      h->err = "component " + std::to_string(tasks[t].k) + ": " + c.err;
     }
   }
   agg.status = worst;
   if (info) {
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+    for (int i = 0; i < n; ++i)
+      if (cudaStreamSynchronize(hs[i]->stream) != cudaSuccess)
+        return fail(hs[i], ST_ERR_CUDA, "stream synchronisation failed");
     *info = agg;
   }
   return worst;
@@ -1532,6 +1789,75 @@ st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* c
          launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
   }
   return check_launch(h, "combine");
+}
+
+st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev) {
+  if (!h || !x_rec || !out_dev || n_rec < 1) return ST_ERR_ARG;
+  if (jt_star < 0 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target time level");
+  for (auto& c : h->comps)
+    if (!c->solved) return fail(h, ST_ERR_STATE, "receiver values before every component is solved");
+  st_status s = build_receivers(h, jt_star, x_rec, n_rec);
+  if (s != ST_OK) return s;
+  const st_handle::RecTables& R = h->rec;
+  launch_receiver_eval(R.comps, (int)h->comps.size(), R.rc, n_rec, R.ncorner, R.tb, R.span, R.nts, out_dev, h->stream);
+  return check_launch(h, "receiver values");
+}
+
+st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int n_rec, const double* d_obs_dev,
+                             int jp, double* J_out, double* dc2_dev, double* dg_dev, st_solve_info* info) {
+  if (!h || !x_rec || !d_obs_dev || n_rec < 1 || !J_out || !dc2_dev || !dg_dev) return ST_ERR_ARG;
+  const st_problem& p = h->prob;
+  if (jt_star < 0 || jt_star > 14 || jp < 0 || jp > 12) return fail(h, ST_ERR_ARG, "bad level");
+  if (p.u0.fn != nullptr) return fail(h, ST_ERR_ARG, "the c^2 gradient is implemented for u0 = 0 only");
+  for (auto& c : h->comps)
+    if (!c->solved) return fail(h, ST_ERR_STATE, "gradient before every component is solved");
+  st_status s = build_receivers(h, jt_star, x_rec, n_rec);
+  if (s != ST_OK) return s;
+  const st_handle::RecTables& R = h->rec;
+  const int ncomp = (int)h->comps.size();
+  launch_receiver_eval(R.comps, ncomp, R.rc, n_rec, R.ncorner, R.tb, R.span, R.nts, R.vals, h->stream);
+  launch_misfit(R.vals, d_obs_dev, R.nts, n_rec, p.T, R.wm, R.J, h->stream);
+  // adjoint right-hand sides G_k = coef_k E_k^T (w * e)
+  for (int c = 0; c < ncomp; ++c) {
+    Component& k = *h->comps[c];
+    const size_t n = (size_t)k.nt * k.nx;
+    if (k.Gadj == nullptr) {
+      k.Gadj = h->alloc<double>(n);
+      k.Lam = h->alloc<double>(n);
+      if (!k.Gadj || !k.Lam) return fail(h, ST_ERR_OOM, "device allocation failed");
+    }
+    ST_CUDA(h, cudaMemsetAsync(k.Gadj, 0, n * sizeof(double), h->stream));
+    launch_adjoint_rhs(R.wm, R.nts, n_rec, R.tb + (size_t)c * R.nts * 3, R.span + (size_t)c * R.nts, k.nt,
+                       R.rc + (size_t)c * n_rec * R.ncorner, R.ncorner, (double)k.coef, k.nx, R.ehat, k.Gadj,
+                       h->stream);
+  }
+  if ((s = check_launch(h, "adjoint right-hand sides")) != ST_OK) return s;
+  // adjoint solves S_k^T L_k = G_k, all components concurrently
+  s = run_solves(h, 0, ncomp, true, info);
+  if (s != ST_OK) return s;
+  // gradient reductions onto the parameter grid
+  ParamGrid pg{};
+  pg.d = p.d;
+  pg.Np = 1 << jp;
+  for (int k = 0; k < 3; ++k) {
+    pg.lo[k] = k < p.d ? p.lo[k] : 0.0;
+    pg.h[k] = k < p.d ? (p.hi[k] - p.lo[k]) / pg.Np : 1.0;
+  }
+  int64_t np = 1;
+  for (int k = 0; k < p.d; ++k) np *= (pg.Np + 1);
+  ST_CUDA(h, cudaMemsetAsync(dc2_dev, 0, np * sizeof(double), h->stream));
+  ST_CUDA(h, cudaMemsetAsync(dg_dev, 0, np * sizeof(double), h->stream));
+  for (int c = 0; c < ncomp; ++c) {
+    Component& k = *h->comps[c];
+    const ElemK ke = element_stiffness(p.d, k.sl->h);
+    launch_grad_c2(k.sl->geo, pg.lo, k.nt, k.td->Bband, k.U, k.Lam, ke, pg, dc2_dev, h->stream);
+    if (p.n_terms >= 1)
+      launch_grad_g(k.sl->geo, pg.lo, k.sl->sc, k.nt, k.td->rhs_coef, k.Lam, R.gv, pg, dg_dev, h->stream);
+  }
+  ST_CUDA(h, cudaMemcpyAsync(h->scalar_h, R.J, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  *J_out = *h->scalar_h;
+  return check_launch(h, "gradient");
 }
 
 st_status st_component_coeffs(st_handle* h, int k, double* host_out) {

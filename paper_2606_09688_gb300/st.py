@@ -76,6 +76,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.st_solve_component.argtypes = [C.c_void_p, C.c_int, C.POINTER(StSolveInfo)]
     lib.st_combine.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     lib.st_combine_subset.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]
+    lib.st_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(StSolveInfo)]
+    lib.st_receiver_values.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+    lib.st_misfit_gradient.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.POINTER(StSolveInfo)]
     lib.st_component_coeffs.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     lib.st_total_dofs.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     lib.st_kernel_launches.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
@@ -261,6 +265,34 @@ class Solver:
         self._check(self._lib.st_combine_subset(self._h, jx_star, jt_star, arr, len(ks), C.c_void_p(out.data_ptr())))
         return out
 
+    def receiver_values(self, jt_star: int, receivers):
+        """u^CF at the receivers (n x d array) and the 2^jt*+1 uniform times, (times, receivers)."""
+        import torch
+        x = np.ascontiguousarray(receivers, dtype=np.float64)
+        out = torch.empty(((1 << jt_star) + 1, len(x)), dtype=torch.float64, device="cuda")
+        self._check(self._lib.st_receiver_values(self._h, jt_star, x.ctypes.data_as(C.c_void_p), len(x),
+                                                  C.c_void_p(out.data_ptr())))
+        return out
+
+    def misfit_gradient(self, jt_star: int, receivers, d_obs, jp: int):
+        """J = 1/2 sum_s w_s sum_r (u^CF - d)^2 and its gradients with respect to nodal c^2 and
+        nodal source factor g on the level-jp grid (st_misfit_gradient).  d_obs: CUDA float64
+        tensor (times, receivers).  Returns (J, dJ/dc2, dJ/dg, StSolveInfo of the adjoint solves)."""
+        import torch
+        x = np.ascontiguousarray(receivers, dtype=np.float64)
+        d_obs = d_obs.to(dtype=torch.float64, device="cuda").contiguous()
+        assert d_obs.shape == ((1 << jt_star) + 1, len(x))
+        npar = ((1 << jp) + 1) ** self.problem.d
+        dc2 = torch.empty(npar, dtype=torch.float64, device="cuda")
+        dg = torch.empty(npar, dtype=torch.float64, device="cuda")
+        J = C.c_double()
+        info = StSolveInfo()
+        self._check(self._lib.st_misfit_gradient(self._h, jt_star, x.ctypes.data_as(C.c_void_p), len(x),
+                                                  C.c_void_p(d_obs.data_ptr()), jp, C.byref(J),
+                                                  C.c_void_p(dc2.data_ptr()), C.c_void_p(dg.data_ptr()),
+                                                  C.byref(info)))
+        return J.value, dc2, dg, info
+
     def coeffs(self, k: int) -> np.ndarray:
         info = self.component(k)
         out = np.empty((info.n_time, info.n_space), dtype=np.float64)
@@ -295,3 +327,20 @@ class Solver:
         a, b = C.c_int64(), C.c_int64()
         self._check(self._lib.st_transfer_bytes(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+def solve_batch(solvers, max_threads: int = 0, sync: bool = True):
+    """Solve all components of several independent Solver instances together
+    (st_solve_batch): (instance, component) pairs largest first over a pool of
+    host threads, each component on its own stream."""
+    solvers = list(solvers)
+    if not solvers:
+        raise ValueError("no solvers")
+    lib = solvers[0]._lib
+    arr = (C.c_void_p * len(solvers))(*[s._h for s in solvers])
+    info = StSolveInfo()
+    code = lib.st_solve_batch(arr, len(solvers), max_threads, C.byref(info) if sync else None)
+    if code != ST_OK:
+        msgs = [lib.st_last_error(s._h).decode() for s in solvers]
+        raise StError(code, next((m for m in msgs if m), "st_solve_batch failed"))
+    return info if sync else None

@@ -165,3 +165,25 @@ def test_combine_subset_parts_add_up_to_the_combination():
     comps, sols = osolve.solve_all(p, method="schur")
     pts, times = osolve.target_grid(p, *target)
     assert _rel(acc, osolve.combine(p, comps, sols, pts, times)) < TOL64
+
+
+def test_solve_batch_matches_separate_solves():
+    """st_solve_batch over several instances gives each instance's own solution."""
+    from paper_2606_09688_gb300 import ST_FP32_IR, Solver, StError, solve_batch
+    probs = W.batch_instances(count=4, seed=5, levels=(6, 7, 8))
+    solvers = [Solver(p, precision=ST_FP32_IR) for p in probs]
+    try:
+        info = solve_batch(solvers, max_threads=8)
+        assert info.status == 0
+        for p, s in zip(probs, solvers):
+            J = p.J + 2 * p.mx
+            tgt = (J - p.mx, J - p.mx)
+            out = s.combine(*tgt).cpu().numpy()
+            comps, sols = osolve.solve_all(p, method="schur")
+            pts, times = osolve.target_grid(p, *tgt)
+            assert _rel(out, osolve.combine(p, comps, sols, pts, times)) < TOL32
+        with pytest.raises(StError):
+            solve_batch([solvers[0], solvers[0]])
+    finally:
+        for s in solvers:
+            s.close()
