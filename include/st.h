@@ -102,6 +102,10 @@ typedef struct {
                            (and a band of at most 256) are solved by the
                            banded direct method, larger ones by multigrid-
                            preconditioned COCG (0 = default 16384) */
+  int autotune;         /* stencil launch shapes (time modes per thread, CTA
+                           size) timed per grid size and mode count at setup,
+                           before the COCG graphs are captured, and kept for the
+                           process: 0 or 1 = on (default), -1 = the built-in rule */
 } st_options;
 
 typedef struct {
@@ -230,6 +234,13 @@ typedef struct {
 } st_kernel_stat;
 st_status st_profile(st_handle* h, int enable);
 st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n_out);
+
+/* Launch shapes chosen by the stencil autotuner so far in this process:
+ * 7 ints per entry (operation 0 apply / 1 residual / 2 Jacobi / 3 first
+ * Jacobi sweep, dimension, element size in bytes, grid nodes, time modes,
+ * modes per thread, threads per CTA), at most max_entries written to out
+ * (may be NULL); *n_out = the number of entries. */
+st_status st_tuned_shapes(int* out, int max_entries, int* n_out);
 
 st_status st_destroy(st_handle* h);
 const char* st_last_error(const st_handle* h);

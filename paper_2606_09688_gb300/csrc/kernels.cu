@@ -4,6 +4,9 @@
 // in common.cuh).  Complex vectors of the time eigenbasis are stored
 // mode-major: element (q, a) at q * stride + a.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <atomic>
 #include <cstdio>
 
@@ -103,7 +106,7 @@ template <typename R> __device__ __forceinline__ cx<R> scaled_div(R s, cx<R> a, 
 // offsets are formed once and applied to every mode of the group, so the
 // per-mode cost is the 3^D loads and the complex FMAs.
 template <int D, typename R, int OP, int MQ>
-__global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
+__global__ void __launch_bounds__(512) k_stencil(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
                                                     const cx<R>* __restrict__ x, const cx<R>* __restrict__ b,
                                                     cx<R>* __restrict__ y, const cx<R>* __restrict__ lam,
                                                     const CocgScal* __restrict__ scal, int nmodes, int64_t stride,
@@ -164,38 +167,119 @@ __global__ void __launch_bounds__(kBlock) k_stencil(Geo g, StencilCoefT<R> sc, c
 template <int D, typename R, int MQ>
 void stencil_dispatch_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                          cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
-                         cudaStream_t s) {
-  dim3 grid(blocks_for(g.nnodes), (nmodes + MQ - 1) / MQ);
+                         int block, cudaStream_t s) {
+  dim3 grid(blocks_for(g.nnodes, block), (nmodes + MQ - 1) / MQ);
   const R om = (R)omega;
   switch (op) {
     case OP_APPLY:
-      k_stencil<D, R, OP_APPLY, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      k_stencil<D, R, OP_APPLY, MQ><<<grid, block, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
       break;
     case OP_RESID:
-      k_stencil<D, R, OP_RESID, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      k_stencil<D, R, OP_RESID, MQ><<<grid, block, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
       break;
     case OP_JACOBI:
-      k_stencil<D, R, OP_JACOBI, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      k_stencil<D, R, OP_JACOBI, MQ><<<grid, block, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
       break;
     default:
-      k_stencil<D, R, OP_JACOBI_ZERO, MQ><<<grid, kBlock, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+      k_stencil<D, R, OP_JACOBI_ZERO, MQ><<<grid, block, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
       break;
   }
 }
 
-// Modes per thread: up to four (two for the 27-point 3D stencil), fewer when
-// the grid alone would not fill the GPU twice over.
+// Launch shapes of the stencil kernels chosen by the autotuner, per
+// (operation, dimension, precision, grid size, mode count); shapes not in
+// the table follow the built-in rule below.
+struct StencilShape {
+  int mq, block;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int64_t, int>, StencilShape> g_tune;
+
+bool tuned_shape(int op, int d, int rsize, int64_t nnodes, int nmodes, StencilShape& out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(op, d, rsize, nnodes, nmodes));
+  if (it == g_tune.end()) return false;
+  out = it->second;
+  return true;
+}
+
+// Built-in rule: up to four modes per thread (two for the 27-point 3D
+// stencil), fewer when the grid alone would not fill the GPU twice over.
+template <int D> StencilShape default_shape(int64_t nnodes, int nmodes) {
+  constexpr int MQMAX = D == 3 ? 2 : 4;
+  const int64_t blocks = (int64_t)blocks_for(nnodes);
+  int mq = 1;
+  while (mq < MQMAX && mq < nmodes && blocks * ((nmodes + 2 * mq - 1) / (2 * mq)) >= 2 * 152) mq *= 2;
+  return StencilShape{mq, kBlock};
+}
+
+template <int D, typename R>
+void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x,
+                          const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
+                          int64_t stride, double omega, StencilShape sh, cudaStream_t s) {
+  if (sh.mq == 4 && D < 3)
+    stencil_dispatch_mq<D, R, (D < 3 ? 4 : 1)>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, sh.block, s);
+  else if (sh.mq >= 2)
+    stencil_dispatch_mq<D, R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, sh.block, s);
+  else
+    stencil_dispatch_mq<D, R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, sh.block, s);
+}
+
 template <int D, typename R>
 void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                       cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
                       cudaStream_t s) {
-  constexpr int MQMAX = D == 3 ? 2 : 4;
-  const int64_t blocks = (int64_t)blocks_for(g.nnodes);
-  int mq = 1;
-  while (mq < MQMAX && mq < nmodes && blocks * ((nmodes + 2 * mq - 1) / (2 * mq)) >= 2 * 152) mq *= 2;
-  if (mq == 4) stencil_dispatch_mq<D, R, (MQMAX >= 4 ? 4 : 1)>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
-  else if (mq == 2) stencil_dispatch_mq<D, R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
-  else stencil_dispatch_mq<D, R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+  StencilShape sh;
+  if (!tuned_shape(op, D, (int)sizeof(R), g.nnodes, nmodes, sh)) sh = default_shape<D>(g.nnodes, nmodes);
+  stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, sh, s);
+}
+
+// Autotuner: time every candidate shape (modes per thread 1, 2, 4 (1, 2 in
+// 3D) x block 128, 256, 512) of one stencil operation on the caller's
+// buffers with CUDA events, the median of three launches each after one
+// untimed launch, and keep the fastest for this (operation, dimension,
+// precision, grid size, mode count).  Synchronises the stream; not to be
+// called during stream capture.  Returns the chosen shape's time in ms.
+template <int D, typename R>
+float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                   cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s) {
+  const int mqs[3] = {1, 2, 4};
+  const int blocks[3] = {128, 256, 512};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  StencilShape best{0, 0};
+  float best_ms = 1e30f;
+  for (int mq : mqs) {
+    if (D == 3 && mq > 2) continue;
+    if (mq > 1 && mq > 2 * nmodes) continue;
+    for (int bk : blocks) {
+      const StencilShape sh{mq, bk};
+      float t[3];
+      stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, nullptr, nmodes, stride, omega, sh, s);
+      for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0, s);
+        stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, nullptr, nmodes, stride, omega, sh, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[r], e0, e1);
+      }
+      std::sort(t, t + 3);
+      if (t[1] < best_ms) {
+        best_ms = t[1];
+        best = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess || best.mq == 0) return -1.f;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[std::make_tuple(op, D, (int)sizeof(R), g.nnodes, nmodes)] = best;
+  return best_ms;
 }
 
 // --------------------------------------------------------- multigrid transfer
@@ -1321,6 +1405,37 @@ void launch_grad_g(const Geo& g, const double* lo, const StencilCoef& sc, int nt
   else k_grad_g<3><<<grid, kBlock, 0, s>>>(g, lo[0], lo[1], lo[2], h0, h1, h2, sc, v, pg, dg);
 }
 
+template <typename R>
+float tune_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                   cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s) {
+  {
+    StencilShape sh;
+    if (tuned_shape(op, g.d, (int)sizeof(R), g.nnodes, nmodes, sh)) return 0.f;  // tuned already
+  }
+  if (g.d == 1) return stencil_tune<1, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
+  if (g.d == 2) return stencil_tune<2, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
+  return stencil_tune<3, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
+}
+
+int tuned_stencil_shapes(int* out, int max_entries) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int n = 0;
+  for (const auto& kv : g_tune) {
+    if (out && n < max_entries) {
+      int* e = out + 7 * n;
+      e[0] = std::get<0>(kv.first);
+      e[1] = std::get<1>(kv.first);
+      e[2] = std::get<2>(kv.first);
+      e[3] = (int)std::get<3>(kv.first);
+      e[4] = std::get<4>(kv.first);
+      e[5] = kv.second.mq;
+      e[6] = kv.second.block;
+    }
+    ++n;
+  }
+  return n;
+}
+
 int64_t kernel_launch_count() { return g_launches.load(); }
 void note_launches(int k) { count(k); }
 
@@ -1344,7 +1459,9 @@ void note_launches(int k) { count(k); }
                                          cudaStream_t);                                                              \
   template void launch_dense_coarse<R>(const cx<R>*, int64_t, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,   \
                                        cudaStream_t);                                                                \
-  template void launch_identity<R>(cx<R>*, int64_t, cudaStream_t);
+  template void launch_identity<R>(cx<R>*, int64_t, cudaStream_t);                                              \
+  template float tune_stencil<R>(int, const Geo&, const StencilCoefT<R>&, const R*, const cx<R>*, const cx<R>*,      \
+                                 cx<R>*, const cx<R>*, int, int64_t, double, cudaStream_t);
 ST_INST(double)
 ST_INST(float)
 #undef ST_INST

@@ -136,6 +136,17 @@ void launch_grad_c2(const Geo& g, const double* lo, int nt, const double* Bband,
 void launch_grad_g(const Geo& g, const double* lo, const StencilCoef& sc, int nt, const double* b, const double* L,
                    double* v, const ParamGrid& pg, double* dg, cudaStream_t s);
 
+// Stencil autotuner: times the launch shapes of one stencil operation on the
+// given buffers (synchronises the stream) and keeps the fastest for later
+// launch_stencil calls with the same operation, dimension, precision, grid
+// size and mode count.  Returns the chosen time in ms, 0 if already tuned, < 0
+// on failure.
+template <typename R>
+float tune_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                   cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s);
+// The tuned shapes: 7 ints per entry (op, d, element size, nodes, modes, modes per thread, block); returns the count.
+int tuned_stencil_shapes(int* out, int max_entries);
+
 // Kernels launched by this process through the wrappers above.
 int64_t kernel_launch_count();
 void note_launches(int k);

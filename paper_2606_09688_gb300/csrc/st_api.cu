@@ -46,6 +46,7 @@ constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
 constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
 constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64
 constexpr double kThetaMG = 1.25;      // coarsest-grid resolution: k h_c <= theta
+constexpr double kShiftMG = 0.5;       // imaginary shift (x |Re lam|) of modes the coarsest grid cannot resolve
 constexpr double kOmega2D = 0.6, kOmega3D = 0.55, kOmega1D = 0.6;
 constexpr int kIterPerGraph = 4;  // COCG iterations between host convergence checks
 
@@ -210,6 +211,11 @@ struct Component {
   double* PhiT = nullptr;
   double* ab = nullptr;
   int* piv = nullptr;
+  // eigenvalues of the multigrid preconditioner per mode (the true ones, or
+  // shifted for modes the coarsest grid cannot resolve)
+  cx<double>* lamP64 = nullptr;
+  cx<float>* lamP32 = nullptr;
+  int nshifted = 0;
   double* abT = nullptr;  // LU of (A + mu B)^T per spatial mode (adjoint systems)
   int* pivT = nullptr;
   int kl = 2, ku = 2;
@@ -819,6 +825,39 @@ st_status setup_component(st_handle* h, Component& c) {
     ST_NEED(h, l.c2f);
     c.mg.push_back(std::move(l));
   }
+  // Preconditioner eigenvalues.  A mode whose wave number k_q = sqrt(-Re lam_q / min c^2)
+  // is not resolved by the coarsest grid (k_q h_c > theta: the V-cycle of K + lam_q M
+  // then stalls) gets the V-cycle of the shifted operator K + (lam_q + i beta |Re lam_q|) M,
+  // which multigrid handles; COCG keeps the true operator, and the shifted
+  // preconditioner is still complex symmetric.
+  {
+    double Lbox = 0.0;
+    for (int k = 0; k < p.d; ++k) Lbox = std::max(Lbox, p.hi[k] - p.lo[k]);
+    const double hc = Lbox / (1 << c.jc);
+    std::vector<cx<double>> lp(c.nsel);
+    std::vector<cx<float>> lpf(c.nsel);
+    c.nshifted = 0;
+    for (int q = 0; q < c.nsel; ++q) {
+      const std::complex<double> l = c.td->eig.lam[q];
+      double im = l.imag();
+      const double kq = std::sqrt(std::max(0.0, -l.real()) / c.sl->c2min);
+      if (!c.direct && kq * hc > kThetaMG) {
+        im += (im >= 0.0 ? 1.0 : -1.0) * kShiftMG * std::fabs(l.real());
+        ++c.nshifted;
+      }
+      lp[q] = mk(l.real(), im);
+      lpf[q] = mk((float)l.real(), (float)im);
+    }
+    if (c.nshifted > 0) {
+      c.lamP64 = h->upload(lp);
+      c.lamP32 = h->upload(lpf);
+      ST_NEED(h, c.lamP64);
+      ST_NEED(h, c.lamP32);
+    } else {
+      c.lamP64 = c.td->lam64;
+      c.lamP32 = c.td->lam32;
+    }
+  }
   const MGLevel& lc = c.mg.back();
   c.bw = (int)band_width(lc.geo);
   c.nrowc = lc.geo.nnodes;
@@ -913,7 +952,7 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   ST_NEED(h, w.bandG);
   ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
   ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
-  launch_band_form<R>(c.Kb, c.Mb, c.td->lam64, w.band, c.bl, c.nsel, c.cs);
+  launch_band_form<R>(c.Kb, c.Mb, c.lamP64, w.band, c.bl, c.nsel, c.cs);
   launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, c.cerr, c.cs);
   if (!c.direct && c.bl.nrow <= kMaxDenseCoarse) {
     // multigrid coarsest level: explicit inverses, column j = the banded
@@ -939,6 +978,9 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
 template <typename R> const cx<R>* lam_of(const TimeData& td);
 template <> const cx<double>* lam_of<double>(const TimeData& td) { return td.lam64; }
 template <> const cx<float>* lam_of<float>(const TimeData& td) { return td.lam32; }
+template <typename R> const cx<R>* plam_of(const Component& c);
+template <> const cx<double>* plam_of<double>(const Component& c) { return c.lamP64; }
+template <> const cx<float>* plam_of<float>(const Component& c) { return c.lamP32; }
 
 double omega_of(int d) { return d == 1 ? kOmega1D : (d == 2 ? kOmega2D : kOmega3D); }
 
@@ -948,7 +990,7 @@ template <typename R>
 cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R>* xb, cx<R>* rtmp) {
   Work<R>& w = work_of<R>(c);
   const MGLevel& lv = c.mg[l];
-  const cx<R>* lam = lam_of<R>(*c.td);
+  const cx<R>* lam = plam_of<R>(c);
   const int64_t n = lv.geo.nnodes;
   cudaStream_t s = c.cs;
   const int L = (int)c.mg.size() - 1;
@@ -1035,6 +1077,38 @@ template <typename R> void cocg_iteration(st_handle* h, Component& c) {
   PROF(h, s, KC_REDUCE, (int64_t)(n), m * n * 2 * cs, m * n * 8.0,
        launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
   PROF(h, s, KC_UPDATE, (int64_t)(n), m * n * 3 * cs, m * n * 8.0, launch_update_p<R>(w.P, z, c.scal, c.nsel, n, n, 0, s));
+}
+
+// Launch shapes of the stencil operations of every multigrid level of a
+// component, timed on its own work buffers (zeroed first) before the COCG
+// iterations are captured; levels below kTuneMinNodes keep the built-in rule.
+// The shapes are kept process-wide, so later handles with the same grids and
+// mode counts reuse them.
+constexpr int64_t kTuneMinNodes = 4096;
+template <typename R> st_status tune_component(st_handle* h, Component& c) {
+  Work<R>& w = work_of<R>(c);
+  const cx<R>* lam = plam_of<R>(c);
+  const int L = (int)c.mg.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    const MGLevel& lv = c.mg[l];
+    const int64_t n = lv.geo.nnodes;
+    if (n < kTuneMinNodes) continue;
+    cx<R>* x = l == 0 ? w.X : w.xa[l];
+    cx<R>* b = l == 0 ? w.G : w.bl[l];
+    cx<R>* y = l == 0 ? w.Wv : w.xb[l];
+    const size_t bytes = (size_t)c.nsel * n * sizeof(cx<R>);
+    ST_CUDAC(c, cudaMemsetAsync(x, 0, bytes, c.cs));
+    ST_CUDAC(c, cudaMemsetAsync(b, 0, bytes, c.cs));
+    const double om = omega_of(lv.geo.d);
+    const R* c2 = c2_of<R>(lv);
+    const int ops[4] = {OP_JACOBI_ZERO, OP_JACOBI, OP_RESID, OP_APPLY};
+    for (int op : ops) {
+      if (op == OP_APPLY && l != 0) continue;
+      if (tune_stencil<R>(op, lv.geo, coef_of<R>(lv), c2, x, b, y, lam, c.nsel, n, om, c.cs) < 0.f)
+        return cfail(c, ST_ERR_CUDA, "stencil autotuning failed");
+    }
+  }
+  return ccheck(c, "autotune");
 }
 
 // Capture the COCG start and kIterPerGraph iterations as CUDA graphs on the
@@ -1263,6 +1337,10 @@ st_status setup_context(st_handle* h, Component& c) {
     st_status s = c.inner64 ? prepare_work<double>(h, c) : prepare_work<float>(h, c);
     if (s != ST_OK) return s;
     if (!c.direct) {
+      if (h->opt.autotune >= 0) {
+        s = c.inner64 ? tune_component<double>(h, c) : tune_component<float>(h, c);
+        if (s != ST_OK) return s;
+      }
       s = c.inner64 ? capture_graphs<double>(h, c) : capture_graphs<float>(h, c);
       if (s != ST_OK) return s;
     }
@@ -1468,6 +1546,7 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   if (!(h->opt.inner_tol >= 0.0 && h->opt.inner_tol < 1.0) || !(h->opt.tol >= 0.0 && h->opt.tol < 1.0))
     return fail(nullptr, ST_ERR_ARG, "tolerances must lie in [0, 1)");
   if (h->opt.max_direct_rows < 0) return fail(nullptr, ST_ERR_ARG, "max_direct_rows must be >= 0");
+  if (h->opt.autotune < -1 || h->opt.autotune > 1) return fail(nullptr, ST_ERR_ARG, "autotune must be -1, 0 or 1");
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->nterm_rows = p.n_terms + 2;
   h->launches0 = kernel_launch_count();
@@ -1858,6 +1937,12 @@ st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
   *J_out = *h->scalar_h;
   return check_launch(h, "gradient");
+}
+
+st_status st_tuned_shapes(int* out, int max_entries, int* n_out) {
+  if (!n_out || max_entries < 0) return ST_ERR_ARG;
+  *n_out = tuned_stencil_shapes(out, max_entries);
+  return ST_OK;
 }
 
 st_status st_component_coeffs(st_handle* h, int k, double* host_out) {

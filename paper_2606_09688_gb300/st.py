@@ -43,7 +43,8 @@ class StProblem(C.Structure):
 
 class StOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("max_sweeps", C.c_int),
-                ("stream", C.c_void_p), ("inner_tol", C.c_double), ("max_direct_rows", C.c_int)]
+                ("stream", C.c_void_p), ("inner_tol", C.c_double), ("max_direct_rows", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class StComponentInfo(C.Structure):
@@ -150,7 +151,8 @@ class Solver:
     """One problem instance behind the C ABI (st_setup .. st_destroy)."""
 
     def __init__(self, problem, precision: int = ST_FP64, tol: float = 0.0, max_iter: int = 0,
-                 max_sweeps: int = 0, stream=None, inner_tol: float = 0.0, max_direct_rows: int = 0):
+                 max_sweeps: int = 0, stream=None, inner_tol: float = 0.0, max_direct_rows: int = 0,
+                 autotune: int = 0):
         import torch
         self._lib = lib()
         p = problem
@@ -189,7 +191,7 @@ class Solver:
             stream = torch.cuda.current_stream()
         self.stream = stream
         opt = StOptions(precision, tol, max_iter, max_sweeps, C.c_void_p(stream.cuda_stream), inner_tol,
-                        max_direct_rows)
+                        max_direct_rows, autotune)
         h = C.c_void_p()
         code = self._lib.st_setup(C.byref(prob), C.byref(opt), C.byref(h))
         if code != ST_OK:
@@ -344,3 +346,15 @@ def solve_batch(solvers, max_threads: int = 0, sync: bool = True):
         msgs = [lib.st_last_error(s._h).decode() for s in solvers]
         raise StError(code, next((m for m in msgs if m), "st_solve_batch failed"))
     return info if sync else None
+
+
+def tuned_shapes():
+    """Stencil launch shapes chosen by the autotuner in this process (st_tuned_shapes):
+    a list of dicts (op, d, elem_bytes, nodes, modes, modes_per_thread, block)."""
+    lib = load_library()
+    n = C.c_int()
+    lib.st_tuned_shapes(None, 0, C.byref(n))
+    buf = (C.c_int * (7 * max(n.value, 1)))()
+    lib.st_tuned_shapes(buf, n.value, C.byref(n))
+    keys = ("op", "d", "elem_bytes", "nodes", "modes", "modes_per_thread", "block")
+    return [dict(zip(keys, buf[7 * i:7 * i + 7])) for i in range(n.value)]

@@ -129,7 +129,7 @@ def test_setup_rejects_bad_tolerances_without_touching_the_gpu():
     prob.c2.fn = cb
     h = C.c_void_p()
     for tol, inner in ((-1e-3, 0.0), (1.5, 0.0), (0.0, -1.0), (0.0, 1.0), (0.0, float("nan"))):
-        opt = B.StOptions(B.ST_FP64, tol, 0, 0, None, inner, 0)
+        opt = B.StOptions(B.ST_FP64, tol, 0, 0, None, inner, 0, 0)
         assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
         assert b"tolerances" in L.st_last_error(None)
         assert h.value is None

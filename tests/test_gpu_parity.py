@@ -187,3 +187,25 @@ def test_solve_batch_matches_separate_solves():
     finally:
         for s in solvers:
             s.close()
+
+
+def test_autotuned_launch_shapes_keep_the_results():
+    """Multigrid on a 127^2 grid (direct limit lowered so that it is not solved
+    directly): with the stencil autotuner on and off the combination matches
+    the oracle, and the tuner has recorded shapes for that grid."""
+    from paper_2606_09688_gb300 import ST_FP32_IR, Solver
+    from paper_2606_09688_gb300.st import tuned_shapes
+    p = W.layered_2d(9, 2)
+    target = (7, 7)
+    comps, sols = osolve.solve_all(p, method="schur")
+    pts, times = osolve.target_grid(p, *target)
+    ref = osolve.combine(p, comps, sols, pts, times)
+    for tune in (-1, 1):
+        with Solver(p, precision=ST_FP32_IR, max_direct_rows=4096, autotune=tune) as s:
+            s.solve(-1)
+            out = s.combine(*target).cpu().numpy()
+        assert _rel(out, ref) < TOL32, (tune, _rel(out, ref))
+    shapes = tuned_shapes()
+    assert any(e["nodes"] == 127 * 127 for e in shapes)
+    for e in shapes:
+        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (128, 256, 512)
