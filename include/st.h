@@ -99,9 +99,9 @@ typedef struct {
                        stops within one refinement sweep (0 = default: 1e-12
                        for FP64 inner solves, 1e-4 for FP32) */
   int max_direct_rows;  /* spatial grids with at most this many unknowns
-                           (and a band of at most 256) are solved by the
+                           (and a band of at most 1024) are solved by the
                            banded direct method, larger ones by multigrid-
-                           preconditioned COCG (0 = default 16384) */
+                           preconditioned COCG (0 = default 32768) */
   int autotune;         /* stencil launch shapes (time modes per thread, CTA
                            size) timed per grid size and mode count at setup,
                            before the COCG graphs are captured, and kept for the

@@ -792,6 +792,13 @@ bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, cons
   } else if (L.bw <= 256) {
     set_smem_attr<R, 8>(smem);
     k_band_solve_w<R, 8><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else if (L.bw <= 512) {
+    set_smem_attr<R, 16>(smem);
+    k_band_solve_w<R, 16><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+  } else if (L.bw <= 1024) {
+    // 3D grids of 31^3 (band 993): the window is 32 registers per lane
+    set_smem_attr<R, 32>(smem);
+    k_band_solve_w<R, 32><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
   } else {
     return false;
   }

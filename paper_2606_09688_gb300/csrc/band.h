@@ -32,7 +32,7 @@ template <typename R>
 void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int* err, cudaStream_t s);
 // x_q = (L D L^T)^{-1} b_q for every active mode (vectors at q * vstride);
 // x may alias nothing but itself.  err[0] = 2 if a copy wait timed out.
-// Returns false when bw exceeds 256 (not supported).
+// Returns false when bw exceeds 1024 (not supported).
 template <typename R>
 bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, const cx<R>* b, cx<R>* x,
                        const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s);

@@ -39,9 +39,9 @@ using namespace st;
 
 namespace {
 
-constexpr int kMaxDirectRows = 16384;  // largest grid solved by the banded direct method
+constexpr int kMaxDirectRows = 32768;  // largest grid solved by the banded direct method (3D: 31^3)
 constexpr int64_t kMaxDenseCoarse = 1024;  // coarsest multigrid grids up to this size use an explicit inverse
-constexpr int kMaxBandWidth = 256;     // widest band the warp solve supports
+constexpr int kMaxBandWidth = 1024;    // widest band the warp solve supports
 constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
 constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
 constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64

@@ -117,6 +117,28 @@ def test_random_medium_3d_small():
     _run(W.random_medium_3d(6, 2, seed=3), 1, (4, 4))
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_random_medium_3d_31cubed_direct_backward_error(prec):
+    """The 31^3 grid (band 993) is solved by the banded direct method; checked by
+    the oracle's own assembly of S and F: the normwise backward error of the
+    GPU's coefficient array is at the refinement target."""
+    import scipy.sparse.linalg as spl
+    from paper_2606_09688_gb300 import Solver
+    p = W.random_medium_3d(7, 2, seed=3)
+    with Solver(p, precision=prec) as s:
+        infos = s.components()
+        k = next(i for i, ci in enumerate(infos) if ci.jx == 5)
+        s.solve(k)
+        U = s.coeffs(k)
+    jx, jt = infos[k].jx, infos[k].jt
+    S = osolve.system_matrix(p, jx, jt)
+    F = osolve.rhs(p, jx, jt)
+    R = F.ravel() - S @ U.ravel()
+    snorm = spl.norm(S, 1)
+    eta = np.linalg.norm(R, 1) / (snorm * np.linalg.norm(U.ravel(), 1) + np.linalg.norm(F.ravel(), 1))
+    assert eta < 1e-13, eta
+
+
 def test_errors_are_reported():
     from paper_2606_09688_gb300 import Solver, StError
     from paper_2606_09688_gb300 import st as B
