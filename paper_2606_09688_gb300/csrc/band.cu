@@ -667,6 +667,123 @@ __global__ void __launch_bounds__(32 * SLOTS) k_band_solve_mw(const cx<R>* __res
   }
 }
 
+// Wide bands (3D grids: bw = n^2 + n + 1 up to 1024): the fixed-slot solve
+// with one warp per 32-row slot of a window padded to W = 32 * NW >= bw rows
+// (NW = ceil(bw / 32) warps; window offsets beyond bw have zero coupling), the
+// band offsets computed at run time instead of unrolled.  Rows are staged in
+// chunks of C rows (C divides 32) by bulk copies; the finished row of each
+// step is passed through shared memory with one block barrier per row.
+template <typename R>
+__global__ void __launch_bounds__(1024) k_band_solve_mwg(const cx<R>* __restrict__ F, const cx<R>* __restrict__ G,
+                                                         BandLayout L, int C, const cx<R>* __restrict__ b,
+                                                         cx<R>* __restrict__ x, const CocgScal* __restrict__ scal,
+                                                         int64_t vstride, int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = blockIdx.x;
+  if (scal != nullptr && !scal[q].active) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5, W = 32 * NW;
+  const int bw = L.bw, ld = L.ld, nrow = (int)L.nrow;
+  const size_t stage_elems = (size_t)C * ld;
+  cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem);
+  cx<R>* stage1 = stage0 + stage_elems;
+  cx<R>* ybuf = stage1 + stage_elems;  // 2 entries, written by other threads between barriers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ybuf + 2);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  unsigned phase[2] = {0u, 0u};
+  const int nchunks = (nrow + C - 1) / C;
+  cx<R>* dst = x + (int64_t)q * vstride;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    const cx<R>* Mq = (pass == 0 ? F : G) + (int64_t)q * L.mstride;
+    const cx<R>* src = pass == 0 ? b + (int64_t)q * vstride : dst;
+    auto chunk = [&](int c, int& klo, int& cnt) {
+      const int k0 = c * C;
+      cnt = min(C, nrow - k0);
+      klo = pass == 0 ? k0 : nrow - k0 - cnt;
+    };
+    auto issue = [&](int c) {
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      cx<R>* st = (c & 1) ? stage1 : stage0;
+      const unsigned bytes = (unsigned)((size_t)cnt * ld * sizeof(cx<R>));
+      mbar_expect_tx(&bar[c & 1], bytes);
+      bulk_g2s(st, Mq + (int64_t)klo * ld, bytes, &bar[c & 1]);
+    };
+    auto at = [&](int rp) -> cx<R> {
+      if (rp >= nrow) return zero;
+      return src[pass == 0 ? rp : nrow - 1 - rp];
+    };
+    if (threadIdx.x == 0) {
+      issue(0);
+      if (nchunks > 1) issue(1);
+    }
+    cx<R> v = at(lane + 32 * warp);
+    cx<R> bcur = at(lane + W), bnext = at(32 + lane + W);  // rows entering during groups 0 and 1
+    if (threadIdx.x == 0) ybuf[1] = v;
+    __syncthreads();
+    cx<R> y = ybuf[1];
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      phase[c & 1] ^= 1u;
+      int klo, cnt;
+      chunk(c, klo, cnt);
+      const cx<R>* st = (c & 1) ? stage1 : stage0;
+      for (int r = 0; r < cnt; ++r) {
+        const int kp = c * C + r, i = kp & 31, g = kp >> 5;
+        if (i == 0 && g > 0) {
+          bcur = bnext;
+          bnext = at(32 * (g + 1) + lane + W);
+        }
+        const int sg = g % NW;
+        const cx<R>* row = st + (size_t)(pass == 0 ? r : cnt - 1 - r) * ld;
+        if (warp == sg && lane == i) {
+          const int k = pass == 0 ? kp : nrow - 1 - kp;
+          dst[k] = pass == 0 ? y * row[0] : y;
+        }
+        int t;
+        cx<R> base = v;
+        if (warp == sg) {
+          if (lane == i) {
+            t = W;  // the row entering the window
+            base = bcur;
+          } else {
+            t = lane - i + (lane < i ? W : 0);
+          }
+        } else {
+          const int dd = warp - sg;
+          t = lane - i + 32 * (dd < 0 ? dd + NW : dd);
+        }
+        const cx<R> a = t <= bw ? row[t] : zero;
+        v = mk<R>(fma(-a.re, y.re, fma(a.im, y.im, base.re)), fma(-a.re, y.im, fma(-a.im, y.re, base.im)));
+        const int nslot = i < 31 ? sg : (sg + 1 == NW ? 0 : sg + 1);
+        if (warp == nslot && lane == ((i + 1) & 31)) ybuf[kp & 1] = v;
+        __syncthreads();
+        y = ybuf[kp & 1];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
+    }
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 2);
+        for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
+      }
+      return;
+    }
+    __syncthreads();
+  }
+}
+
 std::mutex g_attr_mu;  // launches come from several host threads (one per component)
 
 template <typename R, int SLOTS> void set_smem_attr(size_t bytes) {
@@ -683,6 +800,15 @@ template <typename R, int SLOTS> void set_smem_attr_mw(size_t bytes) {
   std::lock_guard<std::mutex> lock(g_attr_mu);
   if (bytes > done) {
     cudaFuncSetAttribute(k_band_solve_mw<R, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
+template <typename R> void set_smem_attr_mwg(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_solve_mwg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     done = bytes;
   }
 }
@@ -792,13 +918,14 @@ bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, cons
   } else if (L.bw <= 256) {
     set_smem_attr<R, 8>(smem);
     k_band_solve_w<R, 8><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
-  } else if (L.bw <= 512) {
-    set_smem_attr<R, 16>(smem);
-    k_band_solve_w<R, 16><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
   } else if (L.bw <= 1024) {
-    // 3D grids of 31^3 (band 993): the window is 32 registers per lane
-    set_smem_attr<R, 32>(smem);
-    k_band_solve_w<R, 32><<<nmodes, 32, smem, s>>>(F, G, L, C, b, x, scal, vstride, err);
+    // wide 3D bands: one warp per 32-row slot of the padded window
+    const int nw = (L.bw + 31) / 32;
+    int cw = 32;
+    while (cw > 1 && 2 * (size_t)cw * L.ld * sizeof(cx<R>) > 160 * 1024) cw >>= 1;
+    const size_t smw = 2 * (size_t)cw * L.ld * sizeof(cx<R>) + 2 * sizeof(cx<R>) + 2 * sizeof(uint64_t);
+    set_smem_attr_mwg<R>(smw);
+    k_band_solve_mwg<R><<<nmodes, 32 * nw, smw, s>>>(F, G, L, cw, b, x, scal, vstride, err);
   } else {
     return false;
   }

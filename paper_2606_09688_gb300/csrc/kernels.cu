@@ -1352,8 +1352,18 @@ template <typename R>
 void launch_dense_coarse(const cx<R>* Ainv, int64_t n, const cx<R>* b, cx<R>* x, const CocgScal* scal, int nmodes,
                          int64_t vstride, cudaStream_t s) {
   count(1);
+  const size_t smem = (size_t)n * sizeof(cx<R>);
+  if (smem > 48 * 1024) {
+    static std::mutex mu;
+    static size_t done = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem > done) {
+      cudaFuncSetAttribute(k_dense_mv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      done = smem;
+    }
+  }
   const dim3 grid((unsigned)((n + kDenseRowsPerBlock - 1) / kDenseRowsPerBlock), nmodes);
-  k_dense_mv<R><<<grid, kBlock, n * sizeof(cx<R>), s>>>(Ainv, (int)n, b, x, scal, vstride);
+  k_dense_mv<R><<<grid, kBlock, smem, s>>>(Ainv, (int)n, b, x, scal, vstride);
 }
 
 template <typename R> void launch_identity(cx<R>* I, int64_t n, cudaStream_t s) {

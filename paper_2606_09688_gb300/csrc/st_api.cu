@@ -40,8 +40,11 @@ using namespace st;
 namespace {
 
 constexpr int kMaxDirectRows = 32768;  // largest grid solved by the banded direct method (3D: 31^3)
-constexpr int64_t kMaxDenseCoarse = 1024;  // coarsest multigrid grids up to this size use an explicit inverse
+constexpr int64_t kCoarseFloor = 1024;     // multigrid coarsening stops at the largest grid of at most this size
+constexpr int64_t kMaxDenseCoarse = 4096;  // coarsest multigrid grids up to this size use an explicit inverse
 constexpr int kMaxBandWidth = 1024;    // widest band the warp solve supports
+constexpr int kMaxCoarseBand = 256;    // widest band of a multigrid coarsest grid
+constexpr int64_t kMaxCoarseRows = 16384;  // largest multigrid coarsest grid
 constexpr int kModeSMaxNx = 1024;      // dense spatial eigenbasis limit
 constexpr int kModeTMaxNt = 129;       // time eigenbasis used up to this many time unknowns
 constexpr double kKappaFP32 = 2.0e5;   // cond(V) above which inner solves stay in FP64
@@ -653,18 +656,26 @@ int choose_coarse(const st_problem& p, const Component& c, int64_t max_direct) {
     kmax = std::max(kmax, std::sqrt(std::max(0.0, -c.td->eig.lam[q].real()) / c.sl->c2min));
   double L = 0.0;
   for (int k = 0; k < p.d; ++k) L = std::max(L, p.hi[k] - p.lo[k]);
-  // no coarser than the largest grid that the explicit coarse inverse takes:
-  // below it, extra levels only add launches to every V-cycle
+  // no coarser than the largest grid of at most kCoarseFloor nodes (its
+  // explicit inverse is cheap): below it, extra levels only add launches to
+  // every V-cycle
   int jc = 2;
-  while (jc + 1 < c.jx && make_geo(p.d, jc + 1).nnodes <= kMaxDenseCoarse) ++jc;
+  while (jc + 1 < c.jx && make_geo(p.d, jc + 1).nnodes <= kCoarseFloor) ++jc;
   while (jc < c.jx && kmax * L / (1 << jc) > kThetaMG) ++jc;
   auto fits = [&](int j) {
     const Geo g = make_geo(p.d, j);
     return g.nnodes <= max_direct && band_width(g) <= kMaxBandWidth;
   };
   if (fits(c.jx)) return c.jx;  // the banded direct solve beats a V-cycle with a large coarse grid
-  int jmax = 1;                 // largest level the banded solve handles
-  while (jmax + 1 <= c.jx && fits(jmax + 1)) ++jmax;
+  // a coarsest multigrid grid is solved once per V-cycle: keep it within the
+  // fast banded solves (band <= kMaxCoarseBand); modes it cannot resolve get
+  // the shifted V-cycle
+  auto fits_coarse = [&](int j) {
+    const Geo g = make_geo(p.d, j);
+    return fits(j) && g.nnodes <= kMaxCoarseRows && band_width(g) <= kMaxCoarseBand;
+  };
+  int jmax = 1;  // largest level the coarse banded solve handles
+  while (jmax + 1 <= c.jx && fits_coarse(jmax + 1)) ++jmax;
   if (jc >= c.jx) return jmax;
   return std::min(jc, jmax);
 }
