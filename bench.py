@@ -252,8 +252,7 @@ def timed_steps(solver, out, target, steps, stream, torch, only=-1):
         if only >= 0:
             solver.solve(only, sync=False)
             continue
-        solver.solve(-1, sync=False)
-        solver.combine(jx, jt, out)
+        solver.solve_combine(jx, jt, out, sync=False)
     end.record(stream)
     end.synchronize()
     return start.elapsed_time(end) / steps
@@ -329,12 +328,14 @@ def run_ours(args):
             setup_s = time.perf_counter() - t0
             dofs = solver.total_dofs
             for _ in range(args.warmup):
-                solver.solve(args.only_component, sync=False)
                 if args.only_component < 0:
-                    solver.combine(target[0], target[1], out)
-            info = solver.solve(args.only_component, sync=True)
+                    solver.solve_combine(target[0], target[1], out, sync=False)
+                else:
+                    solver.solve(args.only_component, sync=False)
             if args.only_component < 0:
-                solver.combine(target[0], target[1], out)
+                _, info = solver.solve_combine(target[0], target[1], out, sync=True)
+            else:
+                info = solver.solve(args.only_component, sync=True)
             barrier()
             l0 = solver.kernel_launches
             clocks = Clocks()
@@ -384,8 +385,7 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
                             max_direct_rows=args.max_direct_rows)
-            s.solve(-1, sync=False)
-            s.combine(target[0], target[1], out)
+            s.solve_combine(target[0], target[1], out, sync=False)
             host_out.copy_(out, non_blocking=True)
             stream.synchronize()
             s.close()
@@ -399,8 +399,7 @@ def run_ours(args):
                 s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
                             max_direct_rows=args.max_direct_rows)
                 tb = time.perf_counter()
-                s.solve(-1, sync=False)
-                s.combine(target[0], target[1], out)
+                s.solve_combine(target[0], target[1], out, sync=False)
                 stream.synchronize()
                 tc = time.perf_counter()
                 host_out.copy_(out, non_blocking=True)

@@ -156,6 +156,14 @@ st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_
  * Requires every component to be solved (ST_ERR_STATE otherwise). */
 st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev);
 
+/* st_solve_component(h, -1) followed by st_combine(h, jx*, jt*, out_dev), with
+ * the combination overlapped with the solves: each level of the hierarchical
+ * combination is enqueued on the handle's stream as soon as the components it
+ * adds have finished, so the coarse levels run while the largest components
+ * are still being solved.  Same result, layout and errors as the two calls;
+ * info (nullable) as for st_solve_component (the call then synchronises). */
+st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_dev, st_solve_info* info);
+
 /* The part of the sum of Eq. (19) contributed by the listed components
  * comps[0..ncomp-1] (distinct indices, each solved), on the same target grid
  * and layout as st_combine.  Eq. (19) is linear in the components, so the

@@ -18,6 +18,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -274,6 +275,7 @@ struct st_handle {
     int* span = nullptr;
     int jmin = 0;
     std::vector<int> first;     // first[lev] = first component of level lev
+    std::vector<int> order;     // component index of each table entry
     std::vector<double*> Y;     // partial sums of the levels below the target
   };
   std::map<std::tuple<int, int, uint64_t>, CombTables> comb;  // per target level pair and component set
@@ -1461,6 +1463,88 @@ ElemK element_stiffness(int d, const double* h) {
   return ke;
 }
 
+// Combination tables for a target level pair and a component set (bit mask):
+// components sorted by their combination level min(jx, jx*), B-spline values
+// of every component at every target time, partial-sum buffers per level.
+// Built once per (target, set) and cached on the handle.
+st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, const st_handle::CombTables** out) {
+  const st_problem& p = h->prob;
+  const int nts = (1 << jt_star) + 1;
+  auto key = std::make_tuple(jx_star, jt_star, mask);
+  auto it = h->comb.find(key);
+  if (it != h->comb.end()) {
+    *out = &it->second;
+    return ST_OK;
+  }
+  std::vector<int> order;
+  for (int c = 0; c < (int)h->comps.size(); ++c)
+    if (mask & (1ull << c)) order.push_back(c);
+  const int nc = (int)order.size();
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return std::min(h->comps[a]->jx, jx_star) < std::min(h->comps[b]->jx, jx_star);
+  });
+  std::vector<CombComp> cc(nc);
+  std::vector<double> tb((size_t)nc * nts * 3);
+  std::vector<int> tsp((size_t)nc * nts);
+  st_handle::CombTables t;
+  t.order = order;
+  t.jmin = jx_star;
+  for (int o = 0; o < nc; ++o) {
+    const Component& k = *h->comps[order[o]];
+    cc[o] = CombComp{k.U, k.sl->lift, k.jx, k.jt, k.coef, 0};
+    const int lev = std::min(k.jx, jx_star);
+    t.jmin = std::min(t.jmin, lev);
+    const int Nt = 1 << k.jt;
+    for (int s = 0; s < nts; ++s) {
+      int span = (k.jt >= jt_star) ? (s << (k.jt - jt_star)) : (s >> (jt_star - k.jt));
+      span = std::min(span, Nt - 1);
+      const double tt = p.T * (double)s / (double)(1 << jt_star);
+      double v[3], d1[3], d2[3];
+      bspline_local(Nt, p.T, span, tt, v, d1, d2);
+      for (int a = 0; a < 3; ++a) tb[((size_t)o * nts + s) * 3 + a] = v[a];
+      tsp[(size_t)o * nts + s] = span;
+    }
+  }
+  t.first.assign(jx_star + 2, nc);
+  for (int o = nc - 1; o >= 0; --o) {
+    const int lev = std::min(cc[o].jx, jx_star);
+    t.first[lev] = o;
+  }
+  for (int lev = jx_star; lev >= 0; --lev) t.first[lev] = std::min(t.first[lev], t.first[lev + 1]);
+  t.comps = h->alloc<CombComp>(nc);
+  t.tb = h->alloc<double>(tb.size());
+  t.span = h->alloc<int>(tsp.size());
+  if (!t.comps || !t.tb || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
+  t.Y.assign(jx_star + 1, nullptr);
+  for (int lev = t.jmin; lev < jx_star; ++lev) {
+    int64_t nsp = 1;
+    for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
+    t.Y[lev] = h->alloc<double>((size_t)nsp * nts);
+    if (!t.Y[lev]) return fail(h, ST_ERR_OOM, "device allocation failed");
+  }
+  ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = &(h->comb[key] = t);
+  return ST_OK;
+}
+
+// One level of the hierarchical combination on the handle's stream.
+void enqueue_comb_level(st_handle* h, const st_handle::CombTables& t, int lev, int jx_star, int jt_star,
+                        double* out_dev) {
+  const st_problem& p = h->prob;
+  const int nts = (1 << jt_star) + 1;
+  const int c0 = t.first[lev], c1 = t.first[lev + 1];
+  const double* Yp = lev > t.jmin ? t.Y[lev - 1] : nullptr;
+  double* Y = lev == jx_star ? out_dev : t.Y[lev];
+  int64_t nsp = 1;
+  for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
+  const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
+  PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, (double)nsp * nts * ((Yp ? 2.0 : 0.0) + 4.0 * (c1 - c0)),
+       launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
+}
+
 // Forward (S U = F) or adjoint (S^T L = G) solves of components k0..k1-1.
 // Component streams start after the work already queued on the handle's
 // stream; independent components run concurrently, one host thread and one
@@ -1810,75 +1894,95 @@ st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* c
     mask |= 1ull << k;
     if (!h->comps[k]->solved) return fail(h, ST_ERR_STATE, "combine before every listed component is solved");
   }
-  const st_problem& p = h->prob;
-  const int nts = (1 << jt_star) + 1;
-  auto key = std::make_tuple(jx_star, jt_star, mask);
-  if (!h->comb.count(key)) {
-    // Components sorted by their combination level min(jx, jx*); B-spline tables
-    // of every component at every target time; partial-sum buffers per level.
-    std::vector<int> order;
-    for (int c = 0; c < (int)h->comps.size(); ++c)
-      if (mask & (1ull << c)) order.push_back(c);
-    const int nc = (int)order.size();
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      return std::min(h->comps[a]->jx, jx_star) < std::min(h->comps[b]->jx, jx_star);
-    });
-    std::vector<CombComp> cc(nc);
-    std::vector<double> tb((size_t)nc * nts * 3);
-    std::vector<int> tsp((size_t)nc * nts);
-    st_handle::CombTables t;
-    t.jmin = jx_star;
-    for (int o = 0; o < nc; ++o) {
-      const Component& k = *h->comps[order[o]];
-      cc[o] = CombComp{k.U, k.sl->lift, k.jx, k.jt, k.coef, 0};
-      const int lev = std::min(k.jx, jx_star);
-      t.jmin = std::min(t.jmin, lev);
-      const int Nt = 1 << k.jt;
-      for (int s = 0; s < nts; ++s) {
-        int span = (k.jt >= jt_star) ? (s << (k.jt - jt_star)) : (s >> (jt_star - k.jt));
-        span = std::min(span, Nt - 1);
-        const double tt = p.T * (double)s / (double)(1 << jt_star);
-        double v[3], d1[3], d2[3];
-        bspline_local(Nt, p.T, span, tt, v, d1, d2);
-        for (int a = 0; a < 3; ++a) tb[((size_t)o * nts + s) * 3 + a] = v[a];
-        tsp[(size_t)o * nts + s] = span;
-      }
-    }
-    t.first.assign(jx_star + 2, nc);
-    for (int o = nc - 1; o >= 0; --o) {
-      const int lev = std::min(cc[o].jx, jx_star);
-      t.first[lev] = o;
-    }
-    for (int lev = jx_star; lev >= 0; --lev) t.first[lev] = std::min(t.first[lev], t.first[lev + 1]);
-    t.comps = h->alloc<CombComp>(nc);
-    t.tb = h->alloc<double>(tb.size());
-    t.span = h->alloc<int>(tsp.size());
-    if (!t.comps || !t.tb || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
-    t.Y.assign(jx_star + 1, nullptr);
-    for (int lev = t.jmin; lev < jx_star; ++lev) {
-      int64_t nsp = 1;
-      for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
-      t.Y[lev] = h->alloc<double>((size_t)nsp * nts);
-      if (!t.Y[lev]) return fail(h, ST_ERR_OOM, "device allocation failed");
-    }
-    ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
-    ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    ST_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->comb[key] = t;
-  }
-  const st_handle::CombTables& t = h->comb[key];
-  for (int lev = t.jmin; lev <= jx_star; ++lev) {
-    const int c0 = t.first[lev], c1 = t.first[lev + 1];
-    const double* Yp = lev > t.jmin ? t.Y[lev - 1] : nullptr;
-    double* Y = lev == jx_star ? out_dev : t.Y[lev];
-    int64_t nsp = 1;
-    for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
-    const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
-    PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, (double)nsp * nts * ((Yp ? 2.0 : 0.0) + 4.0 * (c1 - c0)),
-         launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
-  }
+  const st_handle::CombTables* t = nullptr;
+  st_status s = comb_tables(h, jx_star, jt_star, mask, &t);
+  if (s != ST_OK) return s;
+  for (int lev = t->jmin; lev <= jx_star; ++lev) enqueue_comb_level(h, *t, lev, jx_star, jt_star, out_dev);
   return check_launch(h, "combine");
+}
+
+st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_dev, st_solve_info* info) {
+  if (!h || !out_dev) return ST_ERR_ARG;
+  if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
+  if (h->comps.size() > 64) return fail(h, ST_ERR_ARG, "more than 64 components");
+  const int nc = (int)h->comps.size();
+  const uint64_t mask = nc == 64 ? ~0ull : ((1ull << nc) - 1);
+  const st_handle::CombTables* t = nullptr;
+  st_status s = comb_tables(h, jx_star, jt_star, mask, &t);
+  if (s != ST_OK) return s;
+  // every component on its own stream and host thread; each records its
+  // completion event and reports; the combination levels are enqueued on the
+  // handle's stream level by level, each as soon as the components it adds
+  // have finished (a level also follows the previous one on that stream)
+  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+  for (auto& c : h->comps) {
+    c->err.clear();
+    ST_CUDA(h, cudaStreamWaitEvent(c->cs, h->entry_ev, 0));
+  }
+  std::vector<st_status> st(nc, ST_OK);
+  std::vector<char> done(nc, 0);
+  std::mutex mu;
+  std::condition_variable cv;
+  auto run = [&](int i) {
+    Component& c = *h->comps[i];
+    st_status r = solve_one(h, c, forward_io(c), false);
+    if (r == ST_OK && cudaEventRecord(c.done, c.cs) != cudaSuccess) r = cfail(c, ST_ERR_CUDA, "event record failed");
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      st[i] = r;
+      done[i] = 1;
+    }
+    cv.notify_all();
+  };
+  std::vector<std::thread> pool;
+  if (!h->prof_on) {
+    pool.reserve(nc);
+    for (int i = 0; i < nc; ++i) pool.emplace_back(run, i);
+  }
+  bool failed = false;
+  for (int lev = t->jmin; lev <= jx_star; ++lev) {
+    const int c0 = t->first[lev], c1 = t->first[lev + 1];
+    for (int o = c0; o < c1 && !failed; ++o) {
+      const int k = t->order[o];
+      if (h->prof_on) {
+        run(k);
+      } else {
+        std::unique_lock<std::mutex> lock(mu);
+        cv.wait(lock, [&] { return done[k] != 0; });
+      }
+      if (st[k] != ST_OK) failed = true;
+      else if (cudaStreamWaitEvent(h->stream, h->comps[k]->done, 0) != cudaSuccess) failed = true;
+    }
+    if (failed) break;
+    enqueue_comb_level(h, *t, lev, jx_star, jt_star, out_dev);
+  }
+  for (auto& th : pool) th.join();
+  st_status worst = ST_OK;
+  st_solve_info agg{};
+  for (int i = 0; i < nc; ++i) {
+    Component& c = *h->comps[i];
+    if (!done[i]) continue;  // not started (profiling run stopped at an earlier failure)
+    if (st[i] == ST_OK) {
+      ST_CUDA(h, cudaEventRecord(c.done, c.cs));
+      ST_CUDA(h, cudaStreamWaitEvent(h->stream, c.done, 0));
+    }
+    agg.sweeps = std::max(agg.sweeps, c.info.sweeps);
+    agg.max_inner_iters = std::max(agg.max_inner_iters, c.info.max_inner_iters);
+    agg.rel_residual = std::max(agg.rel_residual, c.info.rel_residual);
+    agg.backward_error = std::max(agg.backward_error, c.info.backward_error);
+    if (st[i] != ST_OK && worst == ST_OK) {
+      worst = st[i];
+      h->err = "component " + std::to_string(i) + ": " + c.err;
+    }
+  }
+  agg.status = worst;
+  if (worst == ST_OK && failed) worst = fail(h, ST_ERR_CUDA, "stream wait failed");
+  if (info) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
+    *info = agg;
+  }
+  if (worst != ST_OK) return worst;
+  return check_launch(h, "solve and combine");
 }
 
 st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev) {

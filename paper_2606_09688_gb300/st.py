@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.st_component.argtypes = [C.c_void_p, C.c_int, C.POINTER(StComponentInfo)]
     lib.st_solve_component.argtypes = [C.c_void_p, C.c_int, C.POINTER(StSolveInfo)]
     lib.st_combine.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.st_solve_combine.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.POINTER(StSolveInfo)]
     lib.st_combine_subset.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]
     lib.st_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(StSolveInfo)]
     lib.st_receiver_values.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
@@ -252,6 +253,20 @@ class Solver:
         assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous() and out.numel() == nts * nsp
         self._check(self._lib.st_combine(self._h, jx_star, jt_star, C.c_void_p(out.data_ptr())))
         return out
+
+    def solve_combine(self, jx_star: int, jt_star: int, out=None, sync: bool = True):
+        """solve(-1) then combine(jx*, jt*), the combination levels overlapped with the
+        solves (st_solve_combine).  Returns (out, StSolveInfo or None)."""
+        import torch
+        nsp = ((1 << jx_star) + 1) ** self.problem.d
+        nts = (1 << jt_star) + 1
+        if out is None:
+            out = torch.empty((nts, nsp), dtype=torch.float64, device="cuda")
+        assert out.dtype == torch.float64 and out.is_cuda and out.is_contiguous() and out.numel() == nts * nsp
+        info = StSolveInfo() if sync else None
+        self._check(self._lib.st_solve_combine(self._h, jx_star, jt_star, C.c_void_p(out.data_ptr()),
+                                               C.byref(info) if sync else None))
+        return out, info
 
     def combine_subset(self, jx_star: int, jt_star: int, comps, out=None):
         """Contribution of the listed components to u^CF on the target grid

@@ -231,3 +231,24 @@ def test_autotuned_launch_shapes_keep_the_results():
     assert any(e["nodes"] == 127 * 127 for e in shapes)
     for e in shapes:
         assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (128, 256, 512)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_combine_overlapped_matches_separate_calls(prec):
+    """st_solve_combine (combination levels enqueued as their components finish)
+    gives the same target values as st_solve_component + st_combine, and the oracle's."""
+    from paper_2606_09688_gb300 import Solver
+    p = W.layered_2d(9, 2)
+    target = (7, 7)
+    with Solver(p, precision=prec) as s:
+        out, info = s.solve_combine(*target)
+        a = out.cpu().numpy()
+        s.solve(-1)
+        b = s.combine(*target).cpu().numpy()
+        a2 = s.solve_combine(*target)[0].cpu().numpy()       # second call on the same handle
+    assert info.status == 0
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(a2 - b)) <= 1e-12 * np.max(np.abs(b))
+    comps, sols = osolve.solve_all(p, method="schur")
+    pts, times = osolve.target_grid(p, *target)
+    assert _rel(a, osolve.combine(p, comps, sols, pts, times)) < (TOL64 if prec == 0 else TOL32)
