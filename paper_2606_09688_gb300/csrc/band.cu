@@ -21,9 +21,13 @@
 #include <cstdint>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "band.h"
 
 namespace st {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -176,6 +180,54 @@ __global__ void k_band_ldlt_win(cx<R>* __restrict__ F, BandLayout L, int RI, int
     }
     __syncthreads();
     slot0 = slot0 + 1 == P ? 0 : slot0 + 1;
+  }
+}
+
+// The global-memory factorisation spread over a cluster of kLdltCluster CTAs
+// per mode (bands whose window does not fit in shared memory): every CTA
+// reads column k, updates its share of the pairs (i, j) (column offsets
+// j = 1 + rank, 1 + rank + kLdltCluster * NP, ...), and one cluster barrier
+// (release / acquire) per column makes the updates visible before column
+// k + 1 is read; rank 0 then stores column k of L (no CTA reads row k again).
+// Every CTA sees the same pivot, so a zero pivot returns all of them together.
+constexpr int kLdltCluster = 4;
+template <typename R>
+__global__ void __cluster_dims__(kLdltCluster, 1, 1) __launch_bounds__(256)
+    k_band_ldlt_cl(cx<R>* __restrict__ F, BandLayout L, int RI, int NP, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* col = reinterpret_cast<cx<R>*>(smem_raw);
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int q = blockIdx.x / kLdltCluster;
+  const int bw = L.bw, ld = L.ld;
+  const int64_t nrow = L.nrow;
+  cx<R>* Fq = F + (int64_t)q * L.mstride;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int i = 1 + tid % RI, p = tid / RI;
+  const int jstep = NP * kLdltCluster;
+  for (int64_t k = 0; k < nrow; ++k) {
+    for (int t = tid; t <= bw; t += nth) col[t] = (k + t < nrow) ? Fq[k * ld + t] : mk<R>(0, 0);
+    __syncthreads();
+    const cx<R> d = col[0];
+    if (!(d.re * d.re + d.im * d.im > R(0))) {
+      if (tid == 0 && rank == 0) atomicExch(err, 1);
+      return;
+    }
+    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
+    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
+    if (i <= m) {
+      const cx<R> u = col[i] * dinv;
+      for (int j = 1 + rank + kLdltCluster * p; j <= i; j += jstep) {
+        cx<R>& tgt = Fq[(k + j) * ld + (i - j)];
+        const cx<R> a = col[j];
+        tgt = mk<R>(fma(-u.re, a.re, fma(u.im, a.im, tgt.re)), fma(-u.re, a.im, fma(-u.im, a.re, tgt.im)));
+      }
+    }
+    cluster.sync();
+    // column k of L (1/d_k in slot 0) by rank 0, after every CTA has read it
+    if (rank == 0)
+      for (int t = tid; t <= m; t += nth) Fq[k * ld + t] = t == 0 ? dinv : col[t] * dinv;
+    __syncthreads();
   }
 }
 
@@ -859,6 +911,9 @@ void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int
     const int RI = (L.bw + 31) / 32 * 32, NP = RI >= 256 ? 1 : 256 / RI;
     set_smem_attr_ldlt<R>(win_bytes);
     k_band_ldlt_win<R><<<nmodes, RI * NP, win_bytes, s>>>(F, L, RI, NP, err);
+  } else if (L.bw <= 256) {
+    const int RI = (L.bw + 31) / 32 * 32, NP = 256 / RI;
+    k_band_ldlt_cl<R><<<nmodes * kLdltCluster, RI * NP, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, RI, NP, err);
   } else {
     k_band_ldlt<R><<<nmodes, 256, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, err);
   }
