@@ -164,6 +164,99 @@ __global__ void __launch_bounds__(512) k_stencil(Geo g, StencilCoefT<R> sc, cons
   }
 }
 
+// 2D variant with the operand staged in shared memory: a CTA takes a
+// 64 x 8 tile of interior nodes and MQ modes, loads the tile's x values with a
+// one-node halo (zero outside the interior) and the c^2 of its 65 x 9 cells
+// with coalesced row loads, then forms each node's row and applies it from
+// shared memory (one global load per node and mode instead of nine).
+constexpr int kTileX = 64, kTileY = 8;
+template <typename R, int OP, int MQ>
+__global__ void __launch_bounds__(256) k_stencil_tile2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
+                                                       const cx<R>* __restrict__ x, const cx<R>* __restrict__ b,
+                                                       cx<R>* __restrict__ y, const cx<R>* __restrict__ lam,
+                                                       const CocgScal* __restrict__ scal, int nmodes,
+                                                       int64_t stride, R omega) {
+  __shared__ cx<R> xs[MQ][kTileY + 2][kTileX + 2];
+  __shared__ R cs[kTileY + 1][kTileX + 1];
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY, q0 = blockIdx.z * MQ;
+  const int n = g.n, N = g.N, tid = threadIdx.x;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int e = tid; e < (kTileX + 1) * (kTileY + 1); e += blockDim.x) {
+    const int hx = e % (kTileX + 1), hy = e / (kTileX + 1);
+    const int cx_ = x0 + hx, cy = y0 + hy;
+    cs[hy][hx] = (cx_ < N && cy < N) ? c2[(int64_t)cy * N + cx_] : R(0);
+  }
+#pragma unroll
+  for (int m = 0; m < MQ; ++m) {
+    const int q = q0 + m;
+    const bool act = q < nmodes && (scal == nullptr || scal[q].active);
+    const cx<R>* xq = x + (int64_t)(act ? q : 0) * stride;
+    for (int e = tid; e < (kTileX + 2) * (kTileY + 2); e += blockDim.x) {
+      const int hx = e % (kTileX + 2), hy = e / (kTileX + 2);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1;
+      xs[m][hy][hx] = (act && gx >= 0 && gx < n && gy >= 0 && gy < n) ? xq[(int64_t)gy * n + gx] : zero;
+    }
+  }
+  __syncthreads();
+  const int tx = tid % kTileX;
+  for (int r = tid / kTileX; r < kTileY; r += blockDim.x / kTileX) {
+    const int ix = x0 + tx, iy = y0 + r;
+    if (ix >= n || iy >= n) continue;
+    const R c00 = cs[r][tx], c10 = cs[r][tx + 1], c01 = cs[r + 1][tx], c11 = cs[r + 1][tx + 1];
+    R kr[9];
+    kr[0] = c00;
+    kr[1] = c00 + c10;
+    kr[2] = c10;
+    kr[3] = c00 + c01;
+    kr[4] = (c00 + c10) + (c01 + c11);
+    kr[5] = c10 + c11;
+    kr[6] = c01;
+    kr[7] = c01 + c11;
+    kr[8] = c11;
+#pragma unroll
+    for (int s2 = 0; s2 < 9; ++s2) kr[s2] *= sc.ke[s2];
+    const int64_t a = (int64_t)iy * n + ix;
+#pragma unroll
+    for (int m = 0; m < MQ; ++m) {
+      const int q = q0 + m;
+      if (q >= nmodes) break;
+      if (scal != nullptr && !scal[q].active) continue;
+      const cx<R> l = lam[q];
+      const cx<R> diag = fma_s(sc.mtot[4], l, mk<R>(kr[4], R(0)));
+      const int64_t base = (int64_t)q * stride + a;
+      cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
+#pragma unroll
+      for (int s2 = 0; s2 < 9; ++s2) {
+        const cx<R> v = xs[m][r + s2 / 3][tx + s2 % 3];
+        ak = fma_s(kr[s2], v, ak);
+        am = fma_s(sc.mtot[s2], v, am);
+      }
+      const cx<R> Ax = fma_c(l, am, ak);
+      if (OP == OP_APPLY) {
+        y[base] = Ax;
+      } else if (OP == OP_RESID) {
+        y[base] = b[base] - Ax;
+      } else {  // OP_JACOBI
+        y[base] = xs[m][r + 1][tx + 1] + scaled_div(omega, b[base] - Ax, diag);
+      }
+    }
+  }
+}
+
+template <typename R, int MQ>
+void stencil_tile2_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                      cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
+                      cudaStream_t s) {
+  const dim3 grid((g.n + kTileX - 1) / kTileX, (g.n + kTileY - 1) / kTileY, (nmodes + MQ - 1) / MQ);
+  const R om = (R)omega;
+  if (op == OP_APPLY)
+    k_stencil_tile2<R, OP_APPLY, MQ><<<grid, 256, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+  else if (op == OP_RESID)
+    k_stencil_tile2<R, OP_RESID, MQ><<<grid, 256, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+  else
+    k_stencil_tile2<R, OP_JACOBI, MQ><<<grid, 256, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om);
+}
+
 template <int D, typename R, int MQ>
 void stencil_dispatch_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                          cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
@@ -213,10 +306,17 @@ template <int D> StencilShape default_shape(int64_t nnodes, int nmodes) {
   return StencilShape{mq, kBlock};
 }
 
+// block == 0 selects the shared-memory tile kernel (2D, operations that read x).
 template <int D, typename R>
 void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x,
                           const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
                           int64_t stride, double omega, StencilShape sh, cudaStream_t s) {
+  if (sh.block == 0 && D == 2 && op != OP_JACOBI_ZERO) {
+    if (sh.mq == 4) stencil_tile2_mq<R, 4>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    else if (sh.mq == 2) stencil_tile2_mq<R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    else stencil_tile2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    return;
+  }
   if (sh.mq == 4 && D < 3)
     stencil_dispatch_mq<D, R, (D < 3 ? 4 : 1)>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, sh.block, s);
   else if (sh.mq >= 2)
@@ -235,7 +335,8 @@ void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* 
 }
 
 // Autotuner: time every candidate shape (modes per thread 1, 2, 4 (1, 2 in
-// 3D) x block 128, 256, 512) of one stencil operation on the caller's
+// 3D) x block 128, 256, 512, and in 2D the shared-memory tile kernel) of one
+// stencil operation on the caller's
 // buffers with CUDA events, the median of three launches each after one
 // untimed launch, and keep the fastest for this (operation, dimension,
 // precision, grid size, mode count).  Synchronises the stream; not to be
@@ -244,7 +345,7 @@ template <int D, typename R>
 float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                    cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s) {
   const int mqs[3] = {1, 2, 4};
-  const int blocks[3] = {128, 256, 512};
+  const int blocks[4] = {128, 256, 512, 0};  // 0: the shared-memory tile kernel (2D)
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -257,6 +358,7 @@ float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
     if (D == 3 && mq > 2) continue;
     if (mq > 1 && mq > 2 * nmodes) continue;
     for (int bk : blocks) {
+      if (bk == 0 && (D != 2 || op == OP_JACOBI_ZERO)) continue;
       const StencilShape sh{mq, bk};
       float t[3];
       stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, nullptr, nmodes, stride, omega, sh, s);
@@ -1425,6 +1527,17 @@ float tune_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
   if (g.d == 1) return stencil_tune<1, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
   if (g.d == 2) return stencil_tune<2, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
   return stencil_tune<3, R>(op, g, sc, c2, x, b, y, lam, nmodes, stride, omega, s);
+}
+
+bool set_stencil_shape(int op, int d, int rsize, int64_t nnodes, int nmodes, int mq, int block) {
+  if (op < 0 || op > 3 || d < 1 || d > 3 || (rsize != 4 && rsize != 8) || nnodes < 1 || nmodes < 1) return false;
+  if (mq != 1 && mq != 2 && mq != 4) return false;
+  if (d == 3 && mq == 4) return false;
+  if (block != 0 && block != 128 && block != 256 && block != 512) return false;
+  if (block == 0 && (d != 2 || op == OP_JACOBI_ZERO)) return false;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[std::make_tuple(op, d, rsize, nnodes, nmodes)] = StencilShape{mq, block};
+  return true;
 }
 
 int tuned_stencil_shapes(int* out, int max_entries) {

@@ -146,6 +146,8 @@ float tune_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
                    cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s);
 // The tuned shapes: 7 ints per entry (op, d, element size, nodes, modes, modes per thread, block); returns the count.
 int tuned_stencil_shapes(int* out, int max_entries);
+// Pin one shape (same fields); false if the shape is not a valid candidate.
+bool set_stencil_shape(int op, int d, int rsize, int64_t nnodes, int nmodes, int mq, int block);
 
 // Kernels launched by this process through the wrappers above.
 int64_t kernel_launch_count();

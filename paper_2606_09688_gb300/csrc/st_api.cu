@@ -2054,6 +2054,12 @@ st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int
   return check_launch(h, "gradient");
 }
 
+st_status st_set_tuned_shape(const int* entry) {
+  if (!entry) return ST_ERR_ARG;
+  return set_stencil_shape(entry[0], entry[1], entry[2], entry[3], entry[4], entry[5], entry[6]) ? ST_OK
+                                                                                                  : ST_ERR_ARG;
+}
+
 st_status st_tuned_shapes(int* out, int max_entries, int* n_out) {
   if (!n_out || max_entries < 0) return ST_ERR_ARG;
   *n_out = tuned_stencil_shapes(out, max_entries);

@@ -373,3 +373,13 @@ def tuned_shapes():
     lib.st_tuned_shapes(buf, n.value, C.byref(n))
     keys = ("op", "d", "elem_bytes", "nodes", "modes", "modes_per_thread", "block")
     return [dict(zip(keys, buf[7 * i:7 * i + 7])) for i in range(n.value)]
+
+
+def set_tuned_shape(entry: dict):
+    """Pin one stencil launch shape (st_set_tuned_shape); entry as returned by tuned_shapes()."""
+    lib = load_library()
+    keys = ("op", "d", "elem_bytes", "nodes", "modes", "modes_per_thread", "block")
+    arr = (C.c_int * 7)(*[int(entry[k]) for k in keys])
+    code = lib.st_set_tuned_shape(arr)
+    if code != ST_OK:
+        raise StError(code, "invalid stencil launch shape")

@@ -213,24 +213,38 @@ def test_solve_batch_matches_separate_solves():
 
 def test_autotuned_launch_shapes_keep_the_results():
     """Multigrid on a 127^2 grid (direct limit lowered so that it is not solved
-    directly): with the stencil autotuner on and off the combination matches
-    the oracle, and the tuner has recorded shapes for that grid."""
-    from paper_2606_09688_gb300 import ST_FP32_IR, Solver
-    from paper_2606_09688_gb300.st import tuned_shapes
+    directly): with the built-in shapes, the autotuned shapes, and every 2D key
+    pinned to the shared-memory tile kernel, the combination matches the oracle."""
+    from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64, Solver, StError
+    from paper_2606_09688_gb300.st import set_tuned_shape, tuned_shapes
     p = W.layered_2d(9, 2)
     target = (7, 7)
     comps, sols = osolve.solve_all(p, method="schur")
     pts, times = osolve.target_grid(p, *target)
     ref = osolve.combine(p, comps, sols, pts, times)
-    for tune in (-1, 1):
-        with Solver(p, precision=ST_FP32_IR, max_direct_rows=4096, autotune=tune) as s:
+
+    def run(prec, tune):
+        with Solver(p, precision=prec, max_direct_rows=4096, autotune=tune) as s:
             s.solve(-1)
-            out = s.combine(*target).cpu().numpy()
-        assert _rel(out, ref) < TOL32, (tune, _rel(out, ref))
+            return s.combine(*target).cpu().numpy()
+    for prec in (ST_FP64, ST_FP32_IR):
+        tol = TOL64 if prec == ST_FP64 else TOL32
+        assert _rel(run(prec, -1), ref) < tol
+        assert _rel(run(prec, 1), ref) < tol
     shapes = tuned_shapes()
     assert any(e["nodes"] == 127 * 127 for e in shapes)
     for e in shapes:
-        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (128, 256, 512)
+        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (0, 128, 256, 512)
+    pinned = 0
+    for e in shapes:
+        if e["d"] == 2 and e["op"] != 3:
+            set_tuned_shape(dict(e, block=0))
+            pinned += 1
+    assert pinned > 0
+    for prec in (ST_FP64, ST_FP32_IR):
+        assert _rel(run(prec, -1), ref) < (TOL64 if prec == ST_FP64 else TOL32)
+    with pytest.raises(StError):
+        set_tuned_shape(dict(shapes[0], modes_per_thread=3))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
