@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstring>
 
 namespace st {
@@ -409,87 +410,193 @@ bool time_eig(const TimeLevel& tl, TimeEig& out) {
   return true;
 }
 
+// Implicit QL iteration with Wilkinson-type shifts on a symmetric tridiagonal
+// matrix (diagonal d, off-diagonal e[i] coupling i and i+1; the method of
+// Bowdler, Martin, Reinsch and Wilkinson, 1968), applying every plane rotation
+// to the rows i, i+1 of ZT (row j of ZT ends as the eigenvector of d[j]).
+static bool tridiag_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& ZT) {
+  const double eps = std::numeric_limits<double>::epsilon();
+  e.resize(n, 0.0);
+  e[n - 1] = 0.0;
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0;; ++iter) {
+      int m = l;
+      for (; m < n - 1; ++m)
+        if (std::fabs(e[m]) <= eps * (std::fabs(d[m]) + std::fabs(d[m + 1]))) break;
+      if (m == l) break;
+      if (iter >= 60) return false;
+      // shift from the eigenvalue of the leading 2 x 2 block nearer d[l]
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
+      double sn = 1.0, cs = 1.0, p = 0.0;
+      bool split = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = sn * e[i], bb = cs * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {  // e[i+1] underflowed: the matrix splits there
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          split = true;
+          break;
+        }
+        sn = f / r;
+        cs = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * sn + 2.0 * cs * bb;
+        p = sn * r;
+        d[i + 1] = g + p;
+        g = cs * r - bb;
+        double* zi = &ZT[(size_t)i * n];
+        double* zj = zi + n;
+        for (int k = 0; k < n; ++k) {
+          const double a = zi[k], c = zj[k];
+          zj[k] = sn * a + cs * c;
+          zi[k] = cs * a - sn * c;
+        }
+      }
+      if (split) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  return true;
+}
+
 bool sym_gen_eig(int n, const std::vector<double>& K, const std::vector<double>& M,
                  std::vector<double>& mu, std::vector<double>& Phi) {
-  // Cholesky M = L L^T, C = L^{-1} K L^{-T}, cyclic Jacobi rotations on C,
-  // Phi = L^{-T} Q so that Phi^T M Phi = I and Phi^T K Phi = diag(mu).
+  // Cholesky M = L L^T and C = L^{-1} K L^{-T}; Householder reduction
+  // C = Q T Q^T to tridiagonal T; implicit QL on T with the rotations
+  // accumulated into Q; Phi = L^{-T} Q so that Phi^T M Phi = I and
+  // Phi^T K Phi = diag(mu).  Row-major throughout, inner loops over rows.
   std::vector<double> L((size_t)n * n, 0.0);
   for (int j = 0; j < n; ++j) {
     double s = M[(size_t)j * n + j];
     for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
     if (s <= 0) return false;
-    const double d = std::sqrt(s);
-    L[(size_t)j * n + j] = d;
+    const double dj = std::sqrt(s);
+    L[(size_t)j * n + j] = dj;
     for (int i = j + 1; i < n; ++i) {
       double t = M[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = t / d;
+      const double* li = &L[(size_t)i * n];
+      const double* lj = &L[(size_t)j * n];
+      for (int k = 0; k < j; ++k) t -= li[k] * lj[k];
+      L[(size_t)i * n + j] = t / dj;
     }
   }
-  // X = L^{-1} K (forward substitution on each column), C = X L^{-T} = (L^{-1} X^T)^T.
-  std::vector<double> X = K;
+  // Y <- L^{-1} Y, row by row (forward substitution on all columns at once)
   auto fwd = [&](std::vector<double>& Y) {
-    for (int c = 0; c < n; ++c)
-      for (int i = 0; i < n; ++i) {
-        double s = Y[(size_t)i * n + c];
-        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * Y[(size_t)k * n + c];
-        Y[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+    for (int i = 0; i < n; ++i) {
+      double* yi = &Y[(size_t)i * n];
+      for (int k = 0; k < i; ++k) {
+        const double lik = L[(size_t)i * n + k];
+        if (lik == 0.0) continue;
+        const double* yk = &Y[(size_t)k * n];
+        for (int c = 0; c < n; ++c) yi[c] -= lik * yk[c];
       }
-  };
-  fwd(X);
-  std::vector<double> Xt((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Xt[(size_t)i * n + j] = X[(size_t)j * n + i];
-  fwd(Xt);
-  std::vector<double> Cm((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Cm[(size_t)i * n + j] = 0.5 * (Xt[(size_t)i * n + j] + Xt[(size_t)j * n + i]);
-  std::vector<double> Qm((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Qm[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        const double v = Cm[(size_t)i * n + j] * Cm[(size_t)i * n + j];
-        tot += v;
-        if (i != j) off += v;
-      }
-    if (off <= 1e-30 * tot) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = Cm[(size_t)p * n + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = Cm[(size_t)p * n + p], aqq = Cm[(size_t)q * n + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = Cm[(size_t)k * n + p], akq = Cm[(size_t)k * n + q];
-          Cm[(size_t)k * n + p] = c * akp - s * akq;
-          Cm[(size_t)k * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = Cm[(size_t)p * n + k], aqk = Cm[(size_t)q * n + k];
-          Cm[(size_t)p * n + k] = c * apk - s * aqk;
-          Cm[(size_t)q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double qkp = Qm[(size_t)k * n + p], qkq = Qm[(size_t)k * n + q];
-          Qm[(size_t)k * n + p] = c * qkp - s * qkq;
-          Qm[(size_t)k * n + q] = s * qkp + c * qkq;
-        }
-      }
-  }
-  mu.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) mu[i] = Cm[(size_t)i * n + i];
-  // Phi = L^{-T} Q (back substitution with L^T on each column).
-  Phi = Qm;
-  for (int c = 0; c < n; ++c)
-    for (int i = n - 1; i >= 0; --i) {
-      double s = Phi[(size_t)i * n + c];
-      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * Phi[(size_t)k * n + c];
-      Phi[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+      const double inv = 1.0 / L[(size_t)i * n + i];
+      for (int c = 0; c < n; ++c) yi[c] *= inv;
     }
+  };
+  std::vector<double> X = K;
+  fwd(X);
+  std::vector<double> C((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) C[(size_t)i * n + j] = X[(size_t)j * n + i];
+  fwd(C);  // C = L^{-1} (L^{-1} K)^T = (L^{-1} K L^{-T})^T
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double v = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+      C[(size_t)i * n + j] = C[(size_t)j * n + i] = v;
+    }
+  // Householder tridiagonalisation: step k maps column k below the
+  // subdiagonal to zero with H_k = I - 2 v v^T acting on indices k+1..n-1.
+  std::vector<double> d(n, 0.0), e(n, 0.0), V((size_t)n * n, 0.0), pv(n), wv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m0 = k + 1, m = n - m0;
+    double* vk = &V[(size_t)k * n];  // v stored at indices k+1..n-1
+    double xn = 0.0;
+    for (int i = m0; i < n; ++i) xn += C[(size_t)k * n + i] * C[(size_t)k * n + i];
+    xn = std::sqrt(xn);
+    const double x0 = C[(size_t)k * n + m0];
+    d[k] = C[(size_t)k * n + k];
+    if (xn == 0.0) {
+      e[k] = 0.0;
+      continue;
+    }
+    const double alpha = x0 > 0 ? -xn : xn;
+    for (int i = m0; i < n; ++i) vk[i] = C[(size_t)k * n + i];
+    vk[m0] -= alpha;
+    double vn = 0.0;
+    for (int i = m0; i < n; ++i) vn += vk[i] * vk[i];
+    vn = std::sqrt(vn);
+    for (int i = m0; i < n; ++i) vk[i] /= vn;
+    // B <- H B H = B - v w^T - w v^T with p = B v, w = 2 (p - (v.p) v)
+    double beta = 0.0;
+    for (int i = m0; i < n; ++i) {
+      const double* ci = &C[(size_t)i * n];
+      double acc = 0.0;
+      for (int j = m0; j < n; ++j) acc += ci[j] * vk[j];
+      pv[i] = acc;
+      beta += vk[i] * acc;
+    }
+    for (int i = m0; i < n; ++i) wv[i] = 2.0 * (pv[i] - beta * vk[i]);
+    for (int i = m0; i < n; ++i) {
+      double* ci = &C[(size_t)i * n];
+      const double vi = vk[i], wi = wv[i];
+      for (int j = m0; j < n; ++j) ci[j] -= vi * wv[j] + wi * vk[j];
+    }
+    e[k] = alpha;
+    (void)m;
+  }
+  if (n >= 2) {
+    d[n - 2] = C[(size_t)(n - 2) * n + (n - 2)];
+    e[n - 2] = C[(size_t)(n - 2) * n + (n - 1)];
+  }
+  d[n - 1] = C[(size_t)(n - 1) * n + (n - 1)];
+  // Q = H_0 H_1 ... H_{n-3}, accumulated from the right end
+  std::vector<double> Q((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int k = n - 3; k >= 0; --k) {
+    const int m0 = k + 1;
+    const double* vk = &V[(size_t)k * n];
+    std::fill(pv.begin(), pv.end(), 0.0);
+    for (int i = m0; i < n; ++i) {
+      const double vi = vk[i];
+      if (vi == 0.0) continue;
+      const double* qi = &Q[(size_t)i * n];
+      for (int j = m0; j < n; ++j) pv[j] += vi * qi[j];
+    }
+    for (int i = m0; i < n; ++i) {
+      const double vi = 2.0 * vk[i];
+      if (vi == 0.0) continue;
+      double* qi = &Q[(size_t)i * n];
+      for (int j = m0; j < n; ++j) qi[j] -= vi * pv[j];
+    }
+  }
+  // eigenvectors of C: Z = Q S; with ZT = Q^T the QL rotations act on rows
+  std::vector<double> ZT((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) ZT[(size_t)j * n + i] = Q[(size_t)i * n + j];
+  if (!tridiag_ql(n, d, e, ZT)) return false;
+  mu = d;
+  // Phi = L^{-T} Z (back substitution, rows from the bottom), Z = ZT^T
+  Phi.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Phi[(size_t)i * n + j] = ZT[(size_t)j * n + i];
+  for (int i = n - 1; i >= 0; --i) {
+    double* pi = &Phi[(size_t)i * n];
+    for (int k = i + 1; k < n; ++k) {
+      const double lki = L[(size_t)k * n + i];
+      if (lki == 0.0) continue;
+      const double* pk = &Phi[(size_t)k * n];
+      for (int c = 0; c < n; ++c) pi[c] -= lki * pk[c];
+    }
+    const double inv = 1.0 / L[(size_t)i * n + i];
+    for (int c = 0; c < n; ++c) pi[c] *= inv;
+  }
   return true;
 }
 

@@ -133,3 +133,29 @@ def test_setup_rejects_bad_tolerances_without_touching_the_gpu():
         assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
         assert b"tolerances" in L.st_last_error(None)
         assert h.value is None
+
+
+def test_sym_gen_eig_on_a_2d_q1_pencil_with_variable_coefficient():
+    """Generalised eigenproblem of a 15^2-node Q1 stiffness (variable diagonal
+    scaling) and mass: eigenvalues against LAPACK, M-orthonormal eigenvectors
+    that diagonalise K."""
+    import scipy.linalg as sla
+    from paper_2606_09688_gb300 import st as B
+    lib = B.lib()
+    n1 = 15
+    n = n1 * n1
+    h = 1.0 / (n1 + 1)
+    T = np.diag(2 * np.ones(n1)) - np.diag(np.ones(n1 - 1), 1) - np.diag(np.ones(n1 - 1), -1)
+    M1 = (h / 6) * (np.diag(4 * np.ones(n1)) + np.diag(np.ones(n1 - 1), 1) + np.diag(np.ones(n1 - 1), -1))
+    K = np.kron(T / h, M1) + np.kron(M1, T / h)
+    M = np.kron(M1, M1)
+    D = np.diag(np.random.default_rng(0).uniform(0.5, 2.0, n))
+    K = D @ K @ D
+    mu = np.zeros(n)
+    Phi = np.zeros((n, n))
+    assert lib.st_host_sym_gen_eig(n, _ptr(np.ascontiguousarray(K)), _ptr(np.ascontiguousarray(M)),
+                                   _ptr(mu), _ptr(Phi)) == 0
+    ref = sla.eigh(K, M, eigvals_only=True)
+    assert np.max(np.abs(np.sort(mu) - ref) / np.abs(ref)) < 1e-11
+    assert np.max(np.abs(Phi.T @ M @ Phi - np.eye(n))) < 1e-12
+    assert np.max(np.abs(Phi.T @ K @ Phi - np.diag(mu))) < 1e-12 * mu.max()
