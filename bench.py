@@ -245,9 +245,10 @@ def csrc_hash():
     return h.hexdigest()
 
 
-def traffic_for(kclass):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary,
-    or None when the kernels have changed since it was taken."""
+def traffic_for(kclass, precision):
+    """DRAM bytes per launch of a kernel class ("<precision>:<class>@<unknowns>")
+    from the committed ncu summary, or None when the kernels have changed since
+    it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -255,7 +256,7 @@ def traffic_for(kclass):
         d = json.load(f)
     if d.get("csrc_sha256") != csrc_hash():
         return None
-    return d.get("bytes_per_launch", {}).get(kclass)
+    return d.get("bytes_per_launch", {}).get(f"{precision}:{kclass}")
 
 
 def timed_steps(solver, out, target, steps, stream, torch, only=-1):
@@ -280,7 +281,7 @@ def roofline(stats, hbm, hbm_src, precision):
     gflops = top["flops"] / (top["ms"] * 1e6)
     alu_peak = FP64_PEAK_GFLOPS if precision == "fp64" else FP32_PEAK_GFLOPS
     fh, fa = gbs / hbm, gflops / alu_peak
-    tr = traffic_for(top["name"])
+    tr = traffic_for(top["name"], precision)
     if fa > fh and precision == "fp64":
         r = {"bound": "alu", "achieved": gflops / 1e3, "peak": alu_peak / 1e3, "unit": "TFLOP/s", "frac": fa,
              "peak_source": "derived: GB300 nominal dense FP64 1.25 TFLOP/s"}
