@@ -159,3 +159,41 @@ def test_sym_gen_eig_on_a_2d_q1_pencil_with_variable_coefficient():
     assert np.max(np.abs(np.sort(mu) - ref) / np.abs(ref)) < 1e-11
     assert np.max(np.abs(Phi.T @ M @ Phi - np.eye(n))) < 1e-12
     assert np.max(np.abs(Phi.T @ K @ Phi - np.diag(mu))) < 1e-12 * mu.max()
+
+
+def test_setup_rejects_bad_solver_options_without_touching_the_gpu():
+    from paper_2606_09688_gb300 import st as B
+    L = B.lib()
+    prob = B.StProblem()
+    prob.d = 1
+    prob.hi[0] = 1.0
+    prob.T = 1.0
+    prob.J = 2
+    prob.mx = 1
+    prob.mt = 1
+
+    def c2(n, x, out, user):
+        for i in range(n):
+            out[i] = 1.0
+        return 0
+    cb = B.SPACE_FN(c2)
+    prob.c2.fn = cb
+    h = C.c_void_p()
+    for max_direct, autotune, msg in ((-1, 0, b"max_direct_rows"), (0, 2, b"autotune"), (0, -2, b"autotune")):
+        opt = B.StOptions(B.ST_FP64, 0.0, 0, 0, None, 0.0, max_direct, autotune)
+        assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
+        assert msg in L.st_last_error(None)
+        assert h.value is None
+
+
+def test_tuned_shape_pinning_validates_the_shape():
+    from paper_2606_09688_gb300 import StError
+    from paper_2606_09688_gb300.st import set_tuned_shape, tuned_shapes
+    good = dict(op=2, d=2, elem_bytes=4, nodes=12345, modes=3, modes_per_thread=2, block=0)
+    set_tuned_shape(good)
+    assert good in tuned_shapes()
+    for bad in (dict(good, modes_per_thread=3), dict(good, block=64), dict(good, d=3, block=0),
+                dict(good, op=3, block=0), dict(good, d=3, modes_per_thread=4, block=256),
+                dict(good, elem_bytes=2), dict(good, nodes=0)):
+        with pytest.raises(StError):
+            set_tuned_shape(bad)
