@@ -94,6 +94,7 @@ def test_gradient_matches_central_differences_on_20_directions():
         rel = abs(fd - an) / max(abs(an), 1e-12)
         worst = max(worst, rel)
         assert rel <= 1e-5, (k, fd, an, rel)
+    print("central differences: worst relative deviation %.2e over 20 directions" % worst)
 
 
 def test_fp32_refinement_gradient_matches_fp64():
