@@ -235,11 +235,12 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
-def csrc_hash():
-    """Hash of every CUDA/C++ source of the library (a changed kernel invalidates ncu numbers)."""
+def csrc_hash(files=None):
+    """Hash of CUDA/C++ sources of the library (all of them, or the listed
+    files): a changed kernel invalidates its ncu numbers."""
     src = os.path.join(ROOT, "paper_2606_09688_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
+    for f in sorted(files if files is not None else os.listdir(src)):
         with open(os.path.join(src, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()
@@ -247,16 +248,17 @@ def csrc_hash():
 
 def traffic_for(kclass, precision):
     """DRAM bytes per launch of a kernel class ("<precision>:<class>@<unknowns>")
-    from the committed ncu summary, or None when the kernels have changed since
-    it was taken."""
+    from the committed ncu summary, or None when the source files that define
+    the kernel have changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("csrc_sha256") != csrc_hash():
+    e = d.get("bytes_per_launch", {}).get(f"{precision}:{kclass}")
+    if not e or e.get("sha256") != csrc_hash(e.get("sources", [])):
         return None
-    return d.get("bytes_per_launch", {}).get(f"{precision}:{kclass}")
+    return e.get("bytes")
 
 
 def timed_steps(solver, out, target, steps, stream, torch, only=-1):

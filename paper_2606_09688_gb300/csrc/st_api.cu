@@ -997,8 +997,10 @@ template <> const cx<float>* plam_of<float>(const Component& c) { return c.lamP3
 
 double omega_of(int d) { return d == 1 ? kOmega1D : (d == 2 ? kOmega2D : kOmega3D); }
 
-// x = B_mg b on level l; two Jacobi sweeps before and after the coarse correction.
-// Returns the buffer holding the result (always xb).
+// x = B_mg b on level l: damped-Jacobi sweeps before and after the coarse
+// correction (one each way for FP64 inner solves, two for FP32); the pre- and
+// post-smoothers are the same symmetric sweep, so B_mg stays complex symmetric.
+// Returns the buffer holding the result.
 template <typename R>
 cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R>* xb, cx<R>* rtmp) {
   Work<R>& w = work_of<R>(c);
@@ -1022,14 +1024,32 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const double om = omega_of(lv.geo.d);
   const R* c2 = c2_of<R>(lv);
   const double cb = (double)lv.geo.ncells * rs;
+  const MGLevel& lc = c.mg[l + 1];
+  const double nc = (double)lc.geo.nnodes;
+  if (sizeof(R) == 8) {
+    // FP64 inner solves are bound by the FP64 pipe: one sweep before and one
+    // after the coarse correction (V(1,1)) costs fewer FP64 operations per
+    // solve than V(2,2) despite one or two more Krylov iterations
+    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 2 * cs + cb, m * n * 30.0,
+         launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, coef_of<R>(lv), c2, nullptr, b, xb, lam, c.scal, c.nsel, n, om, s));
+    PROF(h, s, KC_MG_RESID, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 2.0),
+         launch_stencil<R>(OP_RESID, lv.geo, coef_of<R>(lv), c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
+    PROF(h, s, KC_RESTRICT, (int64_t)(n), m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
+         launch_restrict<R>(lv.geo, lc.geo, rtmp, w.bl[l + 1], c.scal, c.nsel, n, lc.geo.nnodes, s));
+    cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
+    PROF(h, s, KC_PROLONG, (int64_t)(n), m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
+         launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
+    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
+         launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
+    return xa;
+  }
+  // FP32 inner solves are bound by latency and launches: V(2,2), fewer iterations
   PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 2 * cs + cb, m * n * 30.0,
        launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, coef_of<R>(lv), c2, nullptr, b, xa, lam, c.scal, c.nsel, n, om, s));
   PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
        launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xa, b, xb, lam, c.scal, c.nsel, n, om, s));
   PROF(h, s, KC_MG_RESID, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 2.0),
        launch_stencil<R>(OP_RESID, lv.geo, coef_of<R>(lv), c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
-  const MGLevel& lc = c.mg[l + 1];
-  const double nc = (double)lc.geo.nnodes;
   PROF(h, s, KC_RESTRICT, (int64_t)(n), m * (n + nc) * cs, m * nc * 4.0 * ipow3(lv.geo.d),
        launch_restrict<R>(lv.geo, lc.geo, rtmp, w.bl[l + 1], c.scal, c.nsel, n, lc.geo.nnodes, s));
   cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
