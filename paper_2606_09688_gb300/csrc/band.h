@@ -37,4 +37,31 @@ template <typename R>
 bool launch_band_solve(const cx<R>* F, const cx<R>* G, const BandLayout& L, const cx<R>* b, cx<R>* x,
                        const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s);
 
+// Blocked solve for half bandwidths up to 128 (2D grids up to 127^2, 3D up
+// to 7^3).  Rows are grouped into blocks of s = 32 rt >= bw rows, so L is
+// block lower bidiagonal: y_i = L_ii^{-1} (b_i - L_{i,i-1} y_{i-1}) forward and
+// x_i = L_ii^{-T} (D_i^{-1} y_i - L_{i+1,i}^T x_{i+1}) backward.  The inverses
+// X_i = L_ii^{-1} are formed once (FP64 arithmetic), and every operand of the
+// two sweeps is laid out as a stream of 32 x 32 tiles in the order the solve
+// consumes them (per block and phase the triangle's off-diagonal tiles, then
+// its diagonal tiles), which the solve copies into shared memory ahead of use.
+struct BlkLayout {
+  int rt;           // 32-row tiles per block
+  int s;            // rows per block (32 rt)
+  int nb;           // blocks: ceil(nrow / s)
+  int pad;
+  int64_t tstride;  // elements per mode: 4 nb (tiles per phase) 1024
+};
+// Layout for L, or rt = 0 when the bandwidth is too wide for the blocked solve.
+BlkLayout blk_layout(const BandLayout& L);
+// Tile streams S (nmodes x tstride) from the factors F of launch_band_factor.
+template <typename R>
+void launch_band_blk_prepare(const cx<R>* F, const BandLayout& L, const BlkLayout& B, cx<R>* S, int nmodes,
+                             cudaStream_t s);
+// x_q = (L D L^T)^{-1} b_q for every active mode with the blocked solve;
+// x may alias nothing.  err[0] = 2 if a copy wait timed out.
+template <typename R>
+void launch_band_solve_blk(const cx<R>* F, const BandLayout& L, const BlkLayout& B, const cx<R>* S, const cx<R>* b,
+                           cx<R>* x, const CocgScal* scal, int nmodes, int64_t vstride, int* err, cudaStream_t s);
+
 }  // namespace st

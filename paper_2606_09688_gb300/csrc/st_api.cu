@@ -175,6 +175,7 @@ template <typename R> struct Work {
   cx<R>* band = nullptr;               // F factors, nsel x mstride
   cx<R>* bandG = nullptr;              // G (rows of L), nsel x mstride
   cx<R>* cinv = nullptr;               // coarsest-level inverses, nsel x n x n (small coarse grids)
+  cx<R>* blk = nullptr;                // tile streams of the blocked solve, nsel x tstride (bw <= 128)
   bool ready = false;
 };
 
@@ -202,6 +203,7 @@ struct Component {
   int64_t nrowc = 0;
   int bw = 0;
   BandLayout bl{};
+  BlkLayout bk{};  // blocked-solve layout of bl (rt = 0: too wide)
   std::vector<double> Kband, Mband;
   double* Kb = nullptr;
   double* Mb = nullptr;
@@ -967,6 +969,13 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
   launch_band_form<R>(c.Kb, c.Mb, c.lamP64, w.band, c.bl, c.nsel, c.cs);
   launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, c.cerr, c.cs);
+  c.bk = blk_layout(c.bl);
+  if (c.bk.rt > 0 && (c.direct || c.bl.nrow > kMaxDenseCoarse)) {
+    // banded solves in every step: blocked solve with precomputed block inverses
+    w.blk = h->alloc<cx<R>>((size_t)c.nsel * c.bk.tstride);
+    ST_NEED(h, w.blk);
+    launch_band_blk_prepare<R>(w.band, c.bl, c.bk, w.blk, c.nsel, c.cs);
+  }
   if (!c.direct && c.bl.nrow <= kMaxDenseCoarse) {
     // multigrid coarsest level: explicit inverses, column j = the banded
     // solve of e_j (all columns of one mode in one launch, factor shared)
@@ -995,6 +1004,18 @@ template <typename R> const cx<R>* plam_of(const Component& c);
 template <> const cx<double>* plam_of<double>(const Component& c) { return c.lamP64; }
 template <> const cx<float>* plam_of<float>(const Component& c) { return c.lamP32; }
 
+// Banded solve of every active mode of the component's direct grid: the
+// blocked solve when its tile streams exist, the row-by-row kernels otherwise.
+template <typename R>
+bool band_solve(Component& c, const cx<R>* b, cx<R>* x, const CocgScal* scal, int64_t vstride, cudaStream_t s) {
+  Work<R>& w = work_of<R>(c);
+  if (w.blk != nullptr) {
+    launch_band_solve_blk<R>(w.band, c.bl, c.bk, w.blk, b, x, scal, c.nsel, vstride, c.cerr, s);
+    return true;
+  }
+  return launch_band_solve<R>(w.band, w.bandG, c.bl, b, x, scal, c.nsel, vstride, c.cerr, s);
+}
+
 double omega_of(int d) { return d == 1 ? kOmega1D : (d == 2 ? kOmega2D : kOmega3D); }
 
 // x = B_mg b on level l: damped-Jacobi sweeps before and after the coarse
@@ -1017,7 +1038,7 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
            launch_dense_coarse<R>(w.cinv, n, b, xb, c.scal, c.nsel, n, s));
     } else {
       PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs),
-           m * (double)n * c.bw * 16.0, launch_band_solve<R>(w.band, w.bandG, c.bl, b, xb, c.scal, c.nsel, n, c.cerr, s));
+           m * (double)n * c.bw * 16.0, band_solve<R>(c, b, xb, c.scal, n, s));
     }
     return xb;
   }
@@ -1026,7 +1047,7 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   const double cb = (double)lv.geo.ncells * rs;
   const MGLevel& lc = c.mg[l + 1];
   const double nc = (double)lc.geo.nnodes;
-  if (sizeof(R) == 8) {
+  if constexpr (sizeof(R) == 8) {
     // FP64 inner solves are bound by the FP64 pipe: one sweep before and one
     // after the coarse correction (V(1,1)) costs fewer FP64 operations per
     // solve than V(2,2) despite one or two more Krylov iterations
@@ -1184,7 +1205,7 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
   if (c.direct) {
     const double m = c.nsel;
     PROF(h, s, KC_BAND_SOLVE, (int64_t)(n), m * (double)n * (2.0 * c.bl.ld * cs + 3 * cs), m * (double)n * c.bw * 16.0,
-         launch_band_solve<R>(w.band, w.bandG, c.bl, w.G, w.X, nullptr, c.nsel, n, c.cerr, s));
+         band_solve<R>(c, w.G, w.X, nullptr, n, s));
     return ccheck(c, "direct band solve");
   }
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
@@ -1633,6 +1654,37 @@ struct SetupTrace {
   }
 };
 
+// Timeline of one st_solve_combine call on stderr (ms after entry: the end of
+// every component's solve, the start and end of every combination level)
+// when the environment variable ST_STEP_TRACE is set (diagnostics only).
+struct StepTrace {
+  bool on = std::getenv("ST_STEP_TRACE") != nullptr;
+  cudaEvent_t t0 = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::string> what;
+  cudaEvent_t make(const std::string& name) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ev.push_back(e);
+    what.push_back(name);
+    return e;
+  }
+  void report(cudaStream_t s) {
+    if (!on || t0 == nullptr) return;
+    cudaStreamSynchronize(s);
+    for (size_t i = 0; i < ev.size(); ++i) {
+      float ms = -1.0f;
+      if (ev[i] != nullptr && cudaEventElapsedTime(&ms, t0, ev[i]) != cudaSuccess) ms = -1.0f;
+      std::fprintf(stderr, "st_step %-34s %9.3f ms\n", what[i].c_str(), ms);
+    }
+  }
+  ~StepTrace() {
+    for (cudaEvent_t e : ev)
+      if (e != nullptr) cudaEventDestroy(e);
+    if (t0 != nullptr) cudaEventDestroy(t0);
+  }
+};
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -1939,6 +1991,14 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     c->err.clear();
     ST_CUDA(h, cudaStreamWaitEvent(c->cs, h->entry_ev, 0));
   }
+  StepTrace trace;
+  std::vector<cudaEvent_t> comp_ev(nc, nullptr);
+  if (trace.on && cudaEventCreate(&trace.t0) == cudaSuccess) {
+    cudaEventRecord(trace.t0, h->stream);
+    for (int i = 0; i < nc; ++i)
+      comp_ev[i] = trace.make("component (" + std::to_string(h->comps[i]->jx) + "," +
+                              std::to_string(h->comps[i]->jt) + ") solved");
+  }
   std::vector<st_status> st(nc, ST_OK);
   std::vector<char> done(nc, 0);
   std::mutex mu;
@@ -1947,6 +2007,7 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     Component& c = *h->comps[i];
     st_status r = solve_one(h, c, forward_io(c), false);
     if (r == ST_OK && cudaEventRecord(c.done, c.cs) != cudaSuccess) r = cfail(c, ST_ERR_CUDA, "event record failed");
+    if (comp_ev[i] != nullptr) cudaEventRecord(comp_ev[i], c.cs);
     {
       std::lock_guard<std::mutex> lock(mu);
       st[i] = r;
@@ -1974,7 +2035,11 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
       else if (cudaStreamWaitEvent(h->stream, h->comps[k]->done, 0) != cudaSuccess) failed = true;
     }
     if (failed) break;
+    cudaEvent_t lb = trace.t0 ? trace.make("level " + std::to_string(lev) + " combination start") : nullptr;
+    if (lb != nullptr) cudaEventRecord(lb, h->stream);
     enqueue_comb_level(h, *t, lev, jx_star, jt_star, out_dev);
+    cudaEvent_t le = trace.t0 ? trace.make("level " + std::to_string(lev) + " combination end") : nullptr;
+    if (le != nullptr) cudaEventRecord(le, h->stream);
   }
   for (auto& th : pool) th.join();
   st_status worst = ST_OK;
@@ -1997,6 +2062,7 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
   }
   agg.status = worst;
   if (worst == ST_OK && failed) worst = fail(h, ST_ERR_CUDA, "stream wait failed");
+  trace.report(h->stream);
   if (info) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
     *info = agg;
