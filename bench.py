@@ -257,7 +257,7 @@ def traffic_for(kclass, precision):
     with open(path) as f:
         d = json.load(f)
     e = d.get("bytes_per_launch", {}).get(f"{precision}:{kclass}")
-    if not e or e.get("sha256") != csrc_hash(e.get("sources", [])):
+    if not e or not e.get("sources") or e.get("sha256") != csrc_hash(e["sources"]):
         return None
     return e.get("bytes")
 
