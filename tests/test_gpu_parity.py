@@ -108,6 +108,43 @@ def test_layered_medium_2d_level10():
     _run(W.layered_2d(10, 2), 1, (8, 8), method="schur", check_components=False)
 
 
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_layered_n12_sampled_targets_and_backward_errors(prec):
+    """The bench's workload at full size (layered 2D medium, n = 12, m = 2: 17 components,
+    12.1 M space-time DOFs, target (10,10) of 1.08 G values) through st_solve_combine as the
+    bench runs it.  (a) Target values at sampled nodes and times equal the oracle's own
+    evaluation of Eq. (19) from the GPU's component arrays (independent of the combination
+    kernel); (b) the normwise backward error of a blocked direct (7,5), a multigrid (8,4)
+    and a space-eigenbasis (2,10) component, with S and F assembled by the oracle."""
+    import scipy.sparse.linalg as spl
+    import torch
+    from paper_2606_09688_gb300 import Solver
+    p = W.layered_2d(12, 2)
+    target = (10, 10)
+    rng = np.random.default_rng(12)
+    pts, times = osolve.target_grid(p, *target)
+    pi = np.sort(rng.choice(len(pts), 48, replace=False))
+    si = np.sort(rng.choice(len(times), 12, replace=False))
+    with Solver(p, precision=prec) as s:
+        out, info = s.solve_combine(*target)
+        got = out[torch.as_tensor(si, device=out.device)][:, torch.as_tensor(pi, device=out.device)].cpu().numpy()
+        del out
+        infos = s.components()
+        coeffs = [s.coeffs(k) for k in range(len(infos))]
+    assert info.status == 0
+    ref = sum(ci.coef * osolve.evaluate_component(p, ci.jx, ci.jt, U, pts[pi], times[si])
+              for ci, U in zip(infos, coeffs))
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    for jx, jt in ((7, 5), (8, 4), (2, 10)):
+        k = next(i for i, ci in enumerate(infos) if (ci.jx, ci.jt) == (jx, jt))
+        S = osolve.system_matrix(p, jx, jt)
+        F = osolve.rhs(p, jx, jt)
+        U = coeffs[k]
+        R = F.ravel() - S @ U.ravel()
+        eta = np.linalg.norm(R, 1) / (spl.norm(S, 1) * np.linalg.norm(U.ravel(), 1) + np.linalg.norm(F.ravel(), 1))
+        assert eta < 1e-12, ((jx, jt), eta)
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_standing_wave_3d(prec):
     _run(W.standing_wave(3, 6, 2), prec, (4, 4))
