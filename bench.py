@@ -49,8 +49,8 @@ WORKLOADS = {
 }
 METRIC = "space-time DOFs/s (all components, device-timed) + HBM roofline %, FP32+IR vs FP64"
 HBM_FALLBACK = 6800.0
-FP64_PEAK_GFLOPS = 1250.0      # nominal dense FP64 rate of GB300
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07   # SMs x FP32 lanes x 2 flop x max SM GHz
+FP64_NOMINAL_GFLOPS = 1250.0      # nominal dense FP64 rate of GB300 (used only if the probe fails)
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07   # SMs x FP32 lanes x 2 flop x max SM GHz
 FP64_CLASSES = {"combine_level", "st_residual_fp64", "norm_fp64"}
 
 
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--workload", default="layered_2d_n12", choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"],
                     help="precision of the headline value; the other one is reported beside it")
-    ap.add_argument("--skip", default="", help="comma list of: other,profile,e2e,cpu")
+    ap.add_argument("--skip", default="", help="comma list of: other,profile,e2e,cpu,cfg3,batch64")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="inner Krylov tolerance per refinement sweep (0 = library default)")
     ap.add_argument("--max-direct-rows", type=int, default=0,
@@ -80,6 +80,21 @@ def peaks():
             d = json.load(f)
         return float(d.get("hbm_gbs", HBM_FALLBACK)), "measured"
     return HBM_FALLBACK, "fallback"
+
+
+def alu_peaks():
+    """FP64 and FP32 FMA rates of this device measured by st_probe_fma (GFLOP/s),
+    the denominators of the "alu" roofline fractions; nominal figures only if
+    the probe fails."""
+    from paper_2606_09688_gb300.st import probe_fma
+    out = {}
+    for name, prec, nominal in (("fp64", 0, FP64_NOMINAL_GFLOPS), ("fp32", 1, FP32_NOMINAL_GFLOPS)):
+        try:
+            probe_fma(prec, 256)
+            out[name] = (max(probe_fma(prec, 4096) for _ in range(3)), "measured by st_probe_fma")
+        except Exception as e:  # reported in the line's peak_source
+            out[name] = (nominal, f"nominal (probe failed: {str(e)[:60]})")
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -189,6 +204,7 @@ def cpu_baseline(workload):
         return {"value": None, "unit": "DOFs/s", "cores": cores, "kind": "oracle", "sample": "failed: " + r.stderr[-200:]}
     dofs, secs, comps, dofs_p, secs_p = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": dofs_p / secs_p, "unit": "DOFs/s", "cores": cores, "kind": "oracle",
+            "sample_short": f"{len(comps)} smallest components ({dofs} DOFs), solves only",
             "sample": f"{len(comps)} smallest components (<= 300000 DOFs each, {dofs} DOFs) of the same workload, "
                       f"oracle Schur-in-time sparse LU solves spread over {cores} single-threaded processes, "
                       f"{secs_p:.1f} s; combination not included",
@@ -276,7 +292,11 @@ def timed_steps(solver, out, target, steps, stream, torch, only=-1):
     return start.elapsed_time(end) / steps
 
 
-def roofline(stats, hbm, hbm_src, precision):
+def roofline(stats, hbm, hbm_src, precision, alu):
+    """Roofline entry of the kernel class with the largest summed event time:
+    achieved = its algorithmic bytes (or flops) / its event time, against the
+    measured HBM copy rate or the measured FMA rate of its arithmetic type,
+    whichever bounds it by the algorithmic count."""
     if not stats:
         return None
     top = max(stats, key=lambda s: s["ms"])
@@ -284,22 +304,77 @@ def roofline(stats, hbm, hbm_src, precision):
     gflops = top["flops"] / (top["ms"] * 1e6)
     # the combination and the refinement residual compute in FP64 on both paths
     fp64_kernel = precision == "fp64" or top["name"].split("@")[0] in FP64_CLASSES
-    alu_peak = FP64_PEAK_GFLOPS if fp64_kernel else FP32_PEAK_GFLOPS
+    alu_peak, alu_src = alu["fp64" if fp64_kernel else "fp32"]
     fh, fa = gbs / hbm, gflops / alu_peak
     tr = traffic_for(top["name"], precision)
     if fa > fh:
-        src = ("derived: GB300 nominal dense FP64 1.25 TFLOP/s" if fp64_kernel else
-               "derived: GB300 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
         r = {"bound": "alu", "achieved": gflops / 1e3, "peak": alu_peak / 1e3, "unit": "TFLOP/s", "frac": fa,
-             "peak_source": src}
+             "peak_source": ("FP64" if fp64_kernel else "FP32") + " FMA rate " + alu_src}
     else:
         r = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": fh,
              "peak_source": f"{hbm_src} MEASURED_PEAKS.json hbm_gbs"}
     r.update({"traffic": tr, "kernel": top["name"], "launches": top["launches"],
               "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
               "share_of_profiled_time": top["ms"] / sum(s["ms"] for s in stats),
-              "achieved_gbs": gbs, "achieved_gflops": gflops})
+              "achieved_gbs": gbs, "achieved_gflops": gflops, "hbm_frac": fh})
     return r
+
+
+def measure(solver, target, steps, warmup, stream, torch, barrier, maxall, only=-1, clocks=False, profile=True):
+    """Warm-up, then `steps` device-timed steps of one solver; optionally the
+    nvidia-smi clock record of the timed region, a per-kernel-class profile pass
+    and each component timed alone."""
+    out = solver._bench_out
+    for _ in range(warmup):
+        if only < 0:
+            solver.solve_combine(target[0], target[1], out, sync=False)
+        else:
+            solver.solve(only, sync=False)
+    if only < 0:
+        _, info = solver.solve_combine(target[0], target[1], out, sync=True)
+    else:
+        info = solver.solve(only, sync=True)
+    barrier()
+    l0 = solver.kernel_launches
+    ck = Clocks() if clocks else None
+    if ck:
+        ck.start()
+    ms = timed_steps(solver, out, target, steps, stream, torch, only)
+    launches = (solver.kernel_launches - l0) // steps
+    ck = ck.stop(getattr(torch.cuda.get_device_properties(out.device), "pci_bus_id", None)) if ck else None
+    barrier()
+    ms = maxall(ms)
+    stats = comp_ms = None
+    if profile:
+        solver.profile(True)
+        solver.solve(only, sync=False)
+        if only < 0:
+            solver.combine(target[0], target[1], out)
+        stats = solver.profile_read()
+        solver.profile(False)
+        # each component alone (what bounds the step when they overlap)
+        comp_ms = []
+        for k, ci in enumerate(solver.components()):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solver.solve(k, sync=False)
+            b.record(stream)
+            b.synchronize()
+            comp_ms.append({"jx": ci.jx, "jt": ci.jt, "method": ci.method, "modes": ci.n_modes,
+                            "ms": a.elapsed_time(b)})
+    return dict(ms=ms, launches=launches, clocks=ck, stats=stats, comp_ms=comp_ms, sweeps=info.sweeps,
+                inner_iters=info.max_inner_iters, backward_error=info.backward_error,
+                rel_residual=info.rel_residual)
+
+
+def compact_roofline(r):
+    """The roofline keys of the JSON line (the full entry goes to the detail file)."""
+    if r is None:
+        return None
+    out = {k: r[k] for k in ("bound", "unit", "traffic", "kernel") if k in r}
+    for k in ("achieved", "peak", "frac"):
+        out[k] = sig(r[k])
+    return out
 
 
 def run_ours(args):
@@ -321,6 +396,8 @@ def run_ours(args):
     problem = factory()
     stream = torch.cuda.Stream(device=dev)
     hbm, hbm_src = peaks()
+    with torch.cuda.stream(stream):
+        alu = alu_peaks()
     nsp = ((1 << target[0]) + 1) ** problem.d
     nts = (1 << target[1]) + 1
     out = torch.empty((nts, nsp), dtype=torch.float64, device=dev)
@@ -348,51 +425,12 @@ def run_ours(args):
             solver = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
                             max_direct_rows=args.max_direct_rows)
             setup_s = time.perf_counter() - t0
-            dofs = solver.total_dofs
-            for _ in range(args.warmup):
-                if args.only_component < 0:
-                    solver.solve_combine(target[0], target[1], out, sync=False)
-                else:
-                    solver.solve(args.only_component, sync=False)
-            if args.only_component < 0:
-                _, info = solver.solve_combine(target[0], target[1], out, sync=True)
-            else:
-                info = solver.solve(args.only_component, sync=True)
-            barrier()
-            l0 = solver.kernel_launches
-            clocks = Clocks()
-            if prec == args.precision:
-                clocks.start()
-            ms = timed_steps(solver, out, target, args.steps, stream, torch, args.only_component)
-            launches = (solver.kernel_launches - l0) // args.steps
-            ck = clocks.stop(getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", None)) \
-                if prec == args.precision else None
-            barrier()
-            ms = maxall(ms)
-            stats = None
-            comp_ms = None
-            if "profile" not in skip:
-                solver.profile(True)
-                solver.solve(args.only_component, sync=False)
-                if args.only_component < 0:
-                    solver.combine(target[0], target[1], out)
-                stats = solver.profile_read()
-                solver.profile(False)
-                # each component alone (what bounds the step when they overlap)
-                comp_ms = []
-                for k, ci in enumerate(solver.components()):
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    solver.solve(k, sync=False)
-                    b.record(stream)
-                    b.synchronize()
-                    comp_ms.append({"jx": ci.jx, "jt": ci.jt, "method": ci.method, "modes": ci.n_modes,
-                                    "ms": a.elapsed_time(b)})
-            results[prec] = dict(ms=ms, value=dofs * world / (ms / 1e3), dofs=dofs, setup_s=setup_s,
-                                 launches=launches, clocks=ck, stats=stats, comp_ms=comp_ms,
-                                 sweeps=info.sweeps, inner_iters=info.max_inner_iters,
-                                 backward_error=info.backward_error, rel_residual=info.rel_residual,
-                                 solver=solver)
+            solver._bench_out = out
+            r = measure(solver, target, args.steps, args.warmup, stream, torch, barrier, maxall,
+                        only=args.only_component, clocks=(prec == args.precision), profile="profile" not in skip)
+            r.update(value=solver.total_dofs * world / (r["ms"] / 1e3), dofs=solver.total_dofs, setup_s=setup_s,
+                     solver=solver)
+            results[prec] = r
     head = results[args.precision]
     # end to end through the public API with host buffers: setup from the host
     # data (callbacks, uploads), solve, combine, copy the target grid to pinned host memory
@@ -406,7 +444,7 @@ def run_ours(args):
         # for the GPU on its first copy
         with torch.cuda.stream(stream):
             s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
-                            max_direct_rows=args.max_direct_rows)
+                       max_direct_rows=args.max_direct_rows)
             s.solve_combine(target[0], target[1], out, sync=False)
             host_out.copy_(out, non_blocking=True)
             stream.synchronize()
@@ -419,7 +457,7 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 ta = time.perf_counter()
                 s = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
-                            max_direct_rows=args.max_direct_rows)
+                           max_direct_rows=args.max_direct_rows)
                 tb = time.perf_counter()
                 s.solve_combine(target[0], target[1], out, sync=False)
                 stream.synchronize()
@@ -437,37 +475,107 @@ def run_ours(args):
         e2e_s = maxall((time.perf_counter() - t0) / e2e_steps)
         e2e = {"value": head["dofs"] * world / e2e_s, "unit": "DOFs/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "s_per_step": e2e_s,
-               "includes": "st_setup from host callbacks + solve + combine + target grid copied to pinned host",
-               "phases_s": {"setup": phase[0], "solve_combine": phase[1], "copy_to_host": phase[2],
-                            "release": phase[3]}}
+               "phases_s": {k: round(v, 4) for k, v in zip(("setup", "solve_combine", "copy_to_host", "release"),
+                                                           phase)}}
+    for r in results.values():
+        r["solver"].close()
+    del out, host_out
+    torch.cuda.empty_cache()
+
+    # the other single-GPU configurations, compact: the 3D random medium (FP32 + FP64
+    # refinement, its stated precision) and the 64-instance batch
+    subs = {}
+    if "cfg3" not in skip and args.only_component < 0:
+        subs["cfg3"] = sub_3d(args, stream, torch, barrier, maxall, hbm, hbm_src, alu, world)
+    if "batch64" not in skip and world == 1:
+        subs["batch64"] = batch_measure(args, steps=2, warmup=1, compact=True)
     if rank != 0:
         return
     cpu = None if "cpu" in skip else cpu_baseline(args.workload)
-    rl = roofline(head["stats"], hbm, hbm_src, args.precision)
+    rl = roofline(head["stats"], hbm, hbm_src, args.precision, alu)
+    ck = head["clocks"] or {}
     line = {
-        "metric": METRIC, "value": head["value"], "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-        "data": "synthetic (seeded recipe of the workload; no dataset)",
-        "config": {"workload": args.workload, "desc": desc, "target": list(target), "precision": args.precision,
-                   "space_time_dofs": head["dofs"], "l2": "each step writes the 8.6 GB target grid (> L2)",
-                   "parallelism": f"{world} independent instance(s), one per GPU"},
-        "gpu_launches": head["launches"], "clocks": head["clocks"], "roofline": rl, "cpu_baseline": cpu, "e2e": e2e,
-        "setup_s": head["setup_s"], "sweeps": head["sweeps"], "inner_iters": head["inner_iters"],
-        "backward_error": head["backward_error"],
+        "metric": METRIC, "value": sig(head["value"]), "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sig(head["ms"]), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "target": list(target), "dofs": head["dofs"],
+                   "l2": "target grid written each step > L2"},
+        "gpu_launches": head["launches"],
+        "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons")},
+        "roofline": compact_roofline(rl),
+        "cpu_baseline": None if cpu is None else {
+            "value": sig(cpu["value"]), "unit": cpu["unit"], "cores": cpu["cores"], "kind": "oracle",
+            "sample": cpu["sample_short"]},
+        "e2e": None if e2e is None else {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                            "d2h_bytes_per_step")},
+        "backward_error": sig(head["backward_error"], 2),
     }
+    if line["e2e"]:
+        line["e2e"]["value"] = sig(line["e2e"]["value"])
     for prec, r in results.items():
         if prec == args.precision:
             continue
-        line[prec] = {"value": r["value"], "ms_per_step": r["ms"], "setup_s": r["setup_s"],
-                      "gpu_launches": r["launches"], "sweeps": r["sweeps"], "inner_iters": r["inner_iters"],
-                      "backward_error": r["backward_error"], "roofline": roofline(r["stats"], hbm, hbm_src, prec)}
-    line["kernels"] = {prec: r["stats"] for prec, r in results.items()}
-    line["components_alone_ms"] = {prec: r["comp_ms"] for prec, r in results.items()}
-    print(json.dumps(line), flush=True)
+        rr = roofline(r["stats"], hbm, hbm_src, prec, alu)
+        line[prec] = {"value": sig(r["value"]), "ms_per_step": sig(r["ms"]), "backward_error": sig(r["backward_error"], 2),
+                      "roofline_frac": sig(rr["frac"], 3) if rr else None}
+    for name, sub in subs.items():
+        line[name] = {"value": sig(sub["value"]), "ms_per_step": sig(sub["ms_per_step"]),
+                      "backward_error": sig(sub["backward_error"], 2)}
+    detail = {"line": line, "setup_s": {p: r["setup_s"] for p, r in results.items()},
+              "roofline_full": {p: roofline(r["stats"], hbm, hbm_src, p, alu) for p, r in results.items()},
+              "kernels": {p: r["stats"] for p, r in results.items()},
+              "components_alone_ms": {p: r["comp_ms"] for p, r in results.items()},
+              "cpu_baseline": cpu, "e2e": e2e, "alu_peaks": alu, "subresults": subs,
+              "clocks": head["clocks"], "launches": {p: r["launches"] for p, r in results.items()}}
+    write_detail(detail)
+    print(json.dumps(line, separators=(",", ":")), flush=True)
 
 
-def run_batch(args):
+def sig(x, digits=4):
+    """x rounded to `digits` significant figures (None stays None)."""
+    if x is None:
+        return None
+    return float(f"{x:.{digits}g}")
+
+
+def write_detail(detail):
+    """Per-kernel tables and per-component times beside the JSON line (the
+    line itself stays short enough to be read whole)."""
+    d = os.path.join(ROOT, "gpurun_out")
+    try:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "bench_detail.json"), "w") as f:
+            json.dump(detail, f, indent=1, default=str)
+    except OSError as e:
+        print(f"bench: detail not written: {e}", file=sys.stderr)
+
+
+def sub_3d(args, stream, torch, barrier, maxall, hbm, hbm_src, alu, world):
+    """The 3D random-medium configuration (n = 10, m = 3, target (7,7)) in its
+    stated precision, FP32 bulk with FP64 refinement: compact figures."""
+    from paper_2606_09688_gb300 import ST_FP32_IR, Solver
+    factory, target, _ = WORKLOADS["random_medium_3d_n10"]
+    problem = factory()
+    out = torch.empty(((1 << target[1]) + 1, ((1 << target[0]) + 1) ** 3), dtype=torch.float64,
+                      device=torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        solver = Solver(problem, precision=ST_FP32_IR, stream=stream)
+        setup_s = time.perf_counter() - t0
+        solver._bench_out = out
+        r = measure(solver, target, min(args.steps, 5), 2, stream, torch, barrier, maxall, profile=True)
+        dofs = solver.total_dofs
+        solver.close()
+    del out
+    torch.cuda.empty_cache()
+    rl = roofline(r["stats"], hbm, hbm_src, "fp32ir", alu)
+    return {"workload": "random_medium_3d_n10", "precision": "fp32ir", "target": list(target),
+            "space_time_dofs": dofs, "value": dofs * world / (r["ms"] / 1e3), "ms_per_step": r["ms"],
+            "steps": min(args.steps, 5), "warmup": 2, "backward_error": r["backward_error"],
+            "setup_s": round(setup_s, 2), "gpu_launches": r["launches"], "roofline": compact_roofline(rl)}
+
+
+def batch_measure(args, steps, warmup, compact=False):
     """Batching configuration: 64 independent 2D instances (levels n in 8..12,
     random smooth c^2 in [0.5, 2] with a jump, random Gaussian sources), all
     components of all instances solved together by st_solve_batch.  Value =
@@ -475,20 +583,19 @@ def run_batch(args):
     excluded: each instance's own target grid would total ~120 GB)."""
     import torch
     from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64, Solver, solve_batch
-    torch.cuda.set_device(0)
-    code = ST_FP64 if args.precision == "fp64" else ST_FP32_IR
+    code = ST_FP64 if (args.precision == "fp64" and not compact) else ST_FP32_IR
     probs = W.batch_instances(64)
     t0 = time.perf_counter()
     solvers = [Solver(p, precision=code, inner_tol=args.inner_tol, max_direct_rows=args.max_direct_rows)
                for p in probs]
     setup_s = time.perf_counter() - t0
     dofs = sum(s.total_dofs for s in solvers)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         solve_batch(solvers)
     torch.cuda.synchronize()
     times = []
     info = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         info = solve_batch(solvers)
         torch.cuda.synchronize()
@@ -497,17 +604,30 @@ def run_batch(args):
     levels = {}
     for p in probs:
         levels[p.J + 2 * p.mx] = levels.get(p.J + 2 * p.mx, 0) + 1
-    line = {"metric": METRIC, "value": dofs / (ms / 1e3), "unit": "DOFs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if code == ST_FP64 else "f32+f64", "data": "synthetic",
-            "config": {"workload": "batch64", "instances": len(probs), "levels_n": levels, "space_time_dofs": dofs,
-                       "timing": "host wall clock around st_solve_batch (blocking, all streams synchronised)",
-                       "combination": "excluded"},
-            "setup_s": setup_s, "sweeps": info.sweeps, "inner_iters": info.max_inner_iters,
-            "backward_error": info.backward_error}
     for s in solvers:
         s.close()
-    print(json.dumps(line), flush=True)
+    torch.cuda.empty_cache()
+    res = {"value": dofs / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "precision": "fp64" if code == ST_FP64 else "fp32ir", "instances": len(probs), "space_time_dofs": dofs,
+           "backward_error": info.backward_error, "setup_s": round(setup_s, 2),
+           "timing": "host wall clock around st_solve_batch (blocking)"}
+    if compact:
+        return res
+    res["levels_n"] = levels
+    return res
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = batch_measure(args, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["value"], "unit": "DOFs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if r["precision"] == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch64", "instances": r["instances"], "levels_n": r["levels_n"],
+                       "space_time_dofs": r["space_time_dofs"], "timing": r["timing"], "combination": "excluded"},
+            "setup_s": r["setup_s"], "backward_error": r["backward_error"]}
+    print(json.dumps(line, separators=(",", ":")), flush=True)
 
 
 def main():

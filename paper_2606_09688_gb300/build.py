@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libst.so")
-SOURCES = ["kernels.cu", "band.cu", "band_blk.cu", "st_api.cu", "host_math.cpp", "host_abi.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "band.cu", "band_blk.cu", "st_api.cu", "host_math.cpp", "host_abi.cpp", "noalloc.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +31,7 @@ def _stale():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(SRC, f) for f in os.listdir(SRC)]
-    deps += [os.path.join(HERE, "..", "include", f) for f in ("st.h", "st_host.h")]
+    deps += [os.path.join(HERE, "..", "include", f) for f in ("st.h", "st_host.h", "st_probe.h")]
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 

@@ -383,3 +383,19 @@ def set_tuned_shape(entry: dict):
     code = lib.st_set_tuned_shape(arr)
     if code != ST_OK:
         raise StError(code, "invalid stencil launch shape")
+
+
+def probe_fma(precision: int = ST_FP64, iters: int = 4096, stream=None) -> float:
+    """Measured FMA throughput of the current device in GFLOP/s (st_probe_fma):
+    precision ST_FP64 (0) or ST_FP32_IR (1, meaning FP32 arithmetic here)."""
+    import torch
+    lib_ = lib()
+    lib_.st_probe_fma.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p]
+    lib_.st_probe_fma.restype = C.c_int
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    g = C.c_double()
+    code = lib_.st_probe_fma(int(precision), int(iters), C.byref(g), C.c_void_p(stream.cuda_stream))
+    if code != ST_OK:
+        raise StError(code, "st_probe_fma failed")
+    return g.value

@@ -33,7 +33,7 @@ def _ptr(a):
 
 def test_every_declared_symbol_is_exported(lib):
     names = set()
-    for hdr in ("st.h", "st_host.h"):
+    for hdr in ("st.h", "st_host.h", "st_probe.h"):
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names |= set(re.findall(r"\b(st_\w+)\s*\(", text))

@@ -9,6 +9,9 @@ import pytest
 import bench
 
 
+ALU = {"fp64": (1250.0, "measured by st_probe_fma"), "fp32": (80000.0, "measured by st_probe_fma")}
+
+
 def _stats(name, ms, gbytes, gflops, launches=1):
     return [{"name": name, "ms": ms, "launches": launches, "bytes": gbytes * 1e9, "flops": gflops * 1e9}]
 
@@ -16,28 +19,28 @@ def _stats(name, ms, gbytes, gflops, launches=1):
 def test_fp64_only_class_uses_fp64_peak_on_the_mixed_path():
     # the combination computes in FP64 on both paths: 0.86 TFLOP/s is 69 % of 1.25, not of the FP32 rate
     st = _stats("combine_level@1050625", 7.49, 10.77, 6.46)
-    r = bench.roofline(st, 6780.0, "measured", "fp32ir")
+    r = bench.roofline(st, 6780.0, "measured", "fp32ir", ALU)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["peak"] == pytest.approx(1.25)
+    assert r["peak"] == pytest.approx(1.25) and "FP64" in r["peak_source"]
     assert r["frac"] == pytest.approx(6.46 / 7.49 / 1.25, rel=1e-9)
 
 
 def test_fp32_memory_kernel_is_hbm_bound():
     st = _stats("jacobi_smooth@1046529", 1.0, 3.3, 5.0)
-    r = bench.roofline(st, 6780.0, "measured", "fp32ir")
+    r = bench.roofline(st, 6780.0, "measured", "fp32ir", ALU)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["frac"] == pytest.approx(3300.0 / 6780.0, rel=1e-9)
 
 
 def test_fp64_compute_kernel_is_alu_bound():
     st = _stats("jacobi_smooth@1046529", 1.0, 0.7, 1.1)
-    r = bench.roofline(st, 6780.0, "measured", "fp64")
+    r = bench.roofline(st, 6780.0, "measured", "fp64", ALU)
     assert r["bound"] == "alu" and r["frac"] == pytest.approx(1.1 / 1.25, rel=1e-9)
 
 
 def test_dominant_class_is_the_longest_and_share_is_reported():
     st = _stats("a@1", 1.0, 1.0, 0.1) + _stats("b@1", 3.0, 1.0, 0.1, launches=3)
-    r = bench.roofline(st, 6780.0, "measured", "fp64")
+    r = bench.roofline(st, 6780.0, "measured", "fp64", ALU)
     assert r["kernel"] == "b@1" and r["launches"] == 3
     assert r["ms_per_launch"] == pytest.approx(1.0)
     assert r["share_of_profiled_time"] == pytest.approx(0.75)
@@ -75,3 +78,18 @@ def test_committed_traffic_file_parses():
     with open(path) as f:
         d = json.load(f)
     assert isinstance(d.get("bytes_per_launch"), dict) and d.get("how")
+
+
+def test_alu_peak_comes_from_the_probe_figure():
+    st = _stats("combine_level@1050625", 7.49, 10.77, 6.46)
+    alu = {"fp64": (1000.0, "measured by st_probe_fma"), "fp32": (70000.0, "measured by st_probe_fma")}
+    r = bench.roofline(st, 6780.0, "measured", "fp64", alu)
+    assert r["peak"] == pytest.approx(1.0) and r["frac"] == pytest.approx(6.46 / 7.49, rel=1e-9)
+    assert "st_probe_fma" in r["peak_source"]
+
+
+def test_final_line_roofline_is_compact():
+    st = _stats("combine_level@1050625", 7.49, 10.77, 6.46) + _stats("jacobi_smooth@1046529", 1.0, 3.3, 5.0)
+    r = bench.compact_roofline(bench.roofline(st, 6780.0, "measured", "fp64", ALU))
+    assert set(r) == {"bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"}
+    assert len(json.dumps(r)) < 200
