@@ -267,15 +267,23 @@ const char* st_last_error(const st_handle* h);
  * caller-owned component arrays and writes them to caller-owned out_dev
  * ((2^jx*+1)^d x (2^jt*+1) doubles, layout as in st_combine).
  *
- * comps[k]: U = device array of component k's coefficients (n_time x n_space,
- * time-major, the layout of st_component_coeffs), lift = device array of u0 on
- * all (2^jx+1)^d nodes of level jx (NULL if u0 = 0), levels and the
- * combination coefficient (+1 or -1).  At most 64 components.
+ * comps[k]: U = device array of component k's coefficients, (2^jt+1) x
+ * (2^jx-1)^d doubles (time-major, interior nodes x fastest: the layout of
+ * st_component_coeffs), lift = device array of u0 on all (2^jx+1)^d nodes of
+ * level jx, boundary included, x fastest (NULL if u0 = 0), the levels jx, jt
+ * and the combination coefficient (+1 or -1).  At most 64 components.  d must
+ * be the space dimension of the problem the arrays came from: the call cannot
+ * check the arrays' sizes against d, jx and jt, and the caller is responsible
+ * for it (a mismatch makes the kernels read outside the arrays).
  *
  * Scratch: a fixed 32 MiB array in device global memory, part of the library
  * image, so every GPU that loads the library holds it until the process exits.
  * Requests whose tables and partial sums do not fit are rejected with
- * ST_ERR_ARG (so are bad arguments); a failed CUDA call gives ST_ERR_CUDA.
+ * ST_ERR_ARG (so are bad arguments, and a current device ordinal of 64 or
+ * more, beyond the call's per-device cache of the scratch address); a failed
+ * CUDA call or launch gives ST_ERR_CUDA.  A CUDA error already pending on the
+ * calling thread when the call starts is reported as ST_ERR_CUDA before any
+ * work is enqueued and is left pending (not cleared).
  * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine.  Its first call on a device looks up the device address of the
  * scratch array (with that device current); make that first call before any

@@ -36,7 +36,8 @@ void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
 st_status noalloc_scratch(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return ST_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ST_ERR_CUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return ST_ERR_ARG;  // beyond the per-device address cache
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (g_noalloc_ptr[dev] == nullptr) {
     void* p = nullptr;
@@ -118,6 +119,9 @@ extern "C" st_status st_combine_noalloc(const st_comb_input* comps, int ncomp, i
     off = align256(off + sizeof(double) * nsp * nts);
   }
   if (off > kNoallocScratchBytes) return ST_ERR_ARG;  // request exceeds the fixed 32 MiB scratch
+  // An error left pending by earlier work on this thread is not this call's:
+  // report it before enqueueing anything and leave it pending for its owner.
+  if (cudaPeekAtLastError() != cudaSuccess) return ST_ERR_CUDA;
   void* base = nullptr;
   st_status st = noalloc_scratch(&base);
   if (st != ST_OK) return st;
@@ -126,11 +130,12 @@ extern "C" st_status st_combine_noalloc(const st_comb_input* comps, int ncomp, i
   double* tb = reinterpret_cast<double*>(b + off_tb);
   int* span = reinterpret_cast<int*>(b + off_span);
   k_noalloc_tables<<<ncomp, 256, 0, s>>>(nc, ncomp, T, jt_star, nts, cdev, tb, span);
+  if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
   for (int lev = jmin; lev <= jx_star; ++lev) {
     const double* Yp = lev > jmin ? reinterpret_cast<const double*>(b + off_y[lev - 1]) : nullptr;
     double* Y = lev == jx_star ? out_dev : reinterpret_cast<double*>(b + off_y[lev]);
     st::launch_comb_level(d, lev, Yp, cdev, first[lev], first[lev + 1], tb, span, nts, Y, s);
+    if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
   }
-  if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
   return ST_OK;
 }

@@ -3,8 +3,8 @@
 Callers that cannot let the library allocate device memory at call time pass
 their own component arrays and output; the call uses a fixed scratch array
 compiled into the library.  Its output must equal st_combine's on the same
-components, on two calls in a row (the scratch keeps the previous call's
-contents, so the second call checks that nothing stale is read).  This file
+components, on two different calls in a row (the scratch keeps the previous
+call's contents, so the second call checks that nothing stale is read).  This file
 is collected last so that a run stopping at the first failure has already run
 every other test.
 """
@@ -47,10 +47,13 @@ def test_combine_noalloc_matches_st_combine_twice():
     fn.restype = C.c_int
 
     p = W.standing_wave(2, 6, 2)          # u0 != 0, so the lift arrays are exercised
-    target = (5, 4)
+    # two different calls in a row: a target coarser than the finest components
+    # (their values are injected), then a finer one (prolongation); stale tables
+    # or partial sums of the first call would change the second call's result
+    targets = [(3, 3), (5, 4)]
     with Solver(p, precision=ST_FP64) as s:
         s.solve(-1)
-        ref = s.combine(*target).cpu().numpy()
+        refs = [s.combine(*t).cpu().numpy() for t in targets]
         infos = s.components()
         keep = []
         arr = (CombInput * len(infos))()
@@ -59,10 +62,10 @@ def test_combine_noalloc_matches_st_combine_twice():
             lift = torch.from_numpy(_node_values(p, ci.jx, p.u0)).cuda().contiguous()
             keep += [U, lift]
             arr[k] = CombInput(U.data_ptr(), lift.data_ptr(), ci.jx, ci.jt, ci.coef)
+    assert max(ci.jx for ci in infos) > targets[0][0] and max(ci.jx for ci in infos) < targets[1][0]
     stream = torch.cuda.current_stream()
-    out = torch.empty(ref.shape, dtype=torch.float64, device="cuda")
-    for call in range(2):
-        out.fill_(float("nan"))
+    for call, (target, ref) in enumerate(zip(targets, refs)):
+        out = torch.full(ref.shape, float("nan"), dtype=torch.float64, device="cuda")
         code = fn(arr, len(infos), p.d, p.T, target[0], target[1], C.c_void_p(out.data_ptr()),
                   C.c_void_p(stream.cuda_stream))
         assert code == B.ST_OK, (call, code)
