@@ -54,6 +54,57 @@ def system_matrix(problem, jx, jt, sm=None):
     return (sp.kron(sp.csr_matrix(A), sm["M"]) + sp.kron(sp.csr_matrix(B), sm["K"])).tocsc()
 
 
+def apply_system(problem, jx, jt, U, sm=None):
+    """(A (x) M + B (x) K) vec(U) without assembling the space-time matrix.
+
+    With U of shape (n_t, N_x) stored time-major, row i of the product is
+    sum_j A[i,j] M u_j + B[i,j] K u_j (Eq. (30)), i.e. A U M^T + B U K^T in
+    matrix form; M and K are symmetric.  Returns shape (n_t, N_x)."""
+    sm = sm or space.space_matrices(problem, jx)
+    A, B = timemats.time_matrices(jt, problem.T)
+    UM = (sm["M"] @ U.T).T
+    UK = (sm["K"] @ U.T).T
+    return A @ UM + B @ UK
+
+
+def system_norm1(problem, jx, jt, sm=None):
+    """||A (x) M + B (x) K||_1 (largest absolute column sum) without assembling it.
+
+    Column (j, b) holds the blocks A[i,j] M[:, b] + B[i,j] K[:, b] for every
+    time row i, so its absolute sum is sum_i colsum|A[i,j] M + B[i,j] K|[b]."""
+    sm = sm or space.space_matrices(problem, jx)
+    A, B = timemats.time_matrices(jt, problem.T)
+    M, K = sm["M"].tocsr(), sm["K"].tocsr()
+    M.sort_indices()
+    K.sort_indices()
+    # M and K come from the same element connectivity; when their stored
+    # patterns agree the blocks are formed on the value arrays directly
+    same = np.array_equal(M.indptr, K.indptr) and np.array_equal(M.indices, K.indices)
+    nt, n = A.shape[0], M.shape[1]
+    best = 0.0
+    for j in range(nt):
+        col = np.zeros(n)
+        for i in range(nt):
+            if A[i, j] == 0.0 and B[i, j] == 0.0:
+                continue
+            if same:
+                col += np.bincount(M.indices, weights=np.abs(A[i, j] * M.data + B[i, j] * K.data), minlength=n)
+            else:
+                col += np.asarray(abs(A[i, j] * M + B[i, j] * K).sum(axis=0)).ravel()
+        best = max(best, float(col.max()))
+    return best
+
+
+def backward_error(problem, jx, jt, U, F=None, sm=None):
+    """Normwise backward error ||F - S U||_1 / (||S||_1 ||U||_1 + ||F||_1) of a
+    coefficient array U for component (jx, jt), S and F as defined above."""
+    sm = sm or space.space_matrices(problem, jx)
+    if F is None:
+        F = rhs(problem, jx, jt, sm)
+    R = F - apply_system(problem, jx, jt, U, sm)
+    return float(np.abs(R).sum() / (system_norm1(problem, jx, jt, sm) * np.abs(U).sum() + np.abs(F).sum()))
+
+
 def solve_component(problem, jx, jt, F=None, method="lu"):
     """Solve (A (x) M + B (x) K) U = F exactly (up to rounding).
 
