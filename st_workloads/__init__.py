@@ -161,6 +161,24 @@ def layered_2d(n: int = 12, m: int = 2) -> Problem:
                    name=f"layered_2d_n{n}", **levels_nm(n, m))
 
 
+def anisotropic_2d(n: int = 8, m: int = 2) -> Problem:
+    """d = 2 on the non-square box (-0.5, 1.5) x (0, 0.75) (cells 2.67 times wider
+    than tall), final time T = 1.7; c^2 = 1 + 0.5 sin(2 x) cos(3 y) + 0.8 [y > 0.4];
+    u0 = a smooth bump vanishing on the boundary, v0 = 0.5 u0 (x + 0.5);
+    f = Gaussian(sigma 0.1, centre (0.6, 0.3)) x Ricker(peak frequency 3, t0 = 1/3)."""
+    lo, hi = (-0.5, 0.0), (1.5, 0.75)
+
+    def bump(x):
+        s = (x - np.asarray(lo)) / (np.asarray(hi) - np.asarray(lo))
+        return np.prod(np.sin(np.pi * s), axis=1) * np.exp(-((x[:, 0] - 0.3) ** 2))
+
+    return Problem(d=2, lo=lo, hi=hi, T=1.7,
+                   c2=lambda x: 1.0 + 0.5 * np.sin(2 * x[:, 0]) * np.cos(3 * x[:, 1]) + 0.8 * (x[:, 1] > 0.4),
+                   terms=[(gaussian((0.6, 0.3), 0.1), ricker(3.0))],
+                   u0=bump, v0=lambda x: 0.5 * bump(x) * (x[:, 0] + 0.5),
+                   name=f"anisotropic_2d_n{n}", **levels_nm(n, m))
+
+
 def random_fourier_c2(d: int, seed: int, n_modes: int = 16, amp: float = 0.35,
                       kmax: int = 4, lo: float = 0.25, hi: float = 4.0) -> SpaceFn:
     """c^2 = clip(exp(g), lo, hi), g = sum_k a_k cos(2 pi kappa_k . x + phi_k),
