@@ -51,7 +51,8 @@ METRIC = "space-time DOFs/s (all components, device-timed) + HBM roofline %, FP3
 HBM_FALLBACK = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0      # nominal dense FP64 rate of GB300 (used only if the probe fails)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07   # SMs x FP32 lanes x 2 flop x max SM GHz
-FP64_CLASSES = {"combine_level", "st_residual_fp64", "norm_fp64"}
+FP64_CLASSES = {"st_residual_fp64", "norm_fp64"}
+DS_CLASSES = {"combine_level"}      # double-single arithmetic on the FP32 pipe in both precisions
 
 
 def parse():
@@ -70,6 +71,8 @@ def parse():
                     help="largest spatial grid solved by the banded direct method (0 = library default)")
     ap.add_argument("--only-component", type=int, default=-1,
                     help="profiling aid: each step solves only this component (no combination)")
+    ap.add_argument("--target", default="",
+                    help="profiling aid: target levels 'jx,jt' in place of the workload's")
     return ap.parse_args()
 
 
@@ -302,8 +305,10 @@ def roofline(stats, hbm, hbm_src, precision, alu):
     top = max(stats, key=lambda s: s["ms"])
     gbs = top["bytes"] / (top["ms"] * 1e6)
     gflops = top["flops"] / (top["ms"] * 1e6)
-    # the combination and the refinement residual compute in FP64 on both paths
-    fp64_kernel = precision == "fp64" or top["name"].split("@")[0] in FP64_CLASSES
+    # the refinement residual and its norms compute in FP64 on both paths (the
+    # combination computes in double-single arithmetic, on the FP32 pipe)
+    cls = top["name"].split("@")[0]
+    fp64_kernel = cls in FP64_CLASSES or (precision == "fp64" and cls not in DS_CLASSES)
     alu_peak, alu_src = alu["fp64" if fp64_kernel else "fp32"]
     fh, fa = gbs / hbm, gflops / alu_peak
     tr = traffic_for(top["name"], precision)
@@ -393,6 +398,8 @@ def run_ours(args):
     B.build(force=False)
     skip = set(filter(None, args.skip.split(",")))
     factory, target, desc = WORKLOADS[args.workload]
+    if args.target:
+        target = tuple(int(v) for v in args.target.split(","))
     problem = factory()
     stream = torch.cuda.Stream(device=dev)
     hbm, hbm_src = peaks()

@@ -33,6 +33,13 @@ st_status st_host_components(int J, int mx, int mt, int* out);
  * are M-orthonormal eigenvectors). */
 st_status st_host_sym_gen_eig(int n, const double* K, const double* M, double* mu, double* Phi);
 
+/* The FP64 value the combination kernels write for a double-single pair
+ * (h[i], l[i]) (a float pair whose unevaluated sum carries 48 significant
+ * bits, |l| at most half an ulp of h): out[i] = h + l to within one unit in
+ * the last place, formed with integer and float operations only, the same
+ * routine the device runs.  ST_ERR_ARG for n < 0 or null arrays. */
+st_status st_host_ds_to_double(const float* h, const float* l, int64_t n, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libst.so")
 SOURCES = ["kernels.cu", "band.cu", "band_blk.cu", "st_api.cu", "host_math.cpp", "host_abi.cpp", "noalloc.cu",
-           "probe.cu"]
+           "probe.cu", "combine_ds.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -91,6 +91,15 @@ struct CombComp {
 // tspan[c][s] their interval.  Yprev (level j-1, all nodes x nts) may be null.
 void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,
                        const int* tspan, int nts, double* Y, cudaStream_t s);
+// The same level in double-single arithmetic (combine_ds.cu): Yprev and, below
+// the target level, Y hold float pairs (8 bytes per value); the target level
+// (final_level) is written as FP64.  tbw: the B-spline weights as floats,
+// exact (the caller checks that every weight is representable).  L: target
+// times per chunk, from comb_ds_chunk (comp_jt: time levels of the level's
+// components, in table order).
+void launch_comb_level_ds(int d, int j, const void* Yprev, const CombComp* comps, int c0, int c1, const float* tbw,
+                          const int* tspan, int nts, int L, void* Y, bool final_level, cudaStream_t s);
+int comb_ds_chunk(int d, int j, int jt_star, const int* comp_jt, int ncomp_level);
 
 // Coarsest multigrid level by an explicit inverse (grids of at most a few
 // thousand unknowns): x_q = Ainv_q b_q for every active mode, Ainv_q the

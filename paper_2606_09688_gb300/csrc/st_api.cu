@@ -274,6 +274,9 @@ struct st_handle {
   struct CombTables {
     CombComp* comps = nullptr;  // components ordered by combination level
     double* tb = nullptr;
+    float* tbw = nullptr;       // the same weights as floats (exact when ds_ok)
+    bool ds_ok = false;         // every weight exact in FP32: double-single levels
+    std::vector<int> jt;        // time level of each table entry
     int* span = nullptr;
     int jmin = 0;
     std::vector<int> first;     // first[lev] = first component of level lev
@@ -341,6 +344,7 @@ struct st_handle {
     std::lock_guard<std::mutex> lock(alloc_mu);
     void* p = nullptr;
     if (n == 0) n = 1;
+    if (opt.mem_cap_bytes > 0 && mem.bytes + n * sizeof(T) > (size_t)opt.mem_cap_bytes) return nullptr;
     if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
@@ -877,6 +881,8 @@ st_status setup_component(st_handle* h, Component& c) {
   c.bw = (int)band_width(lc.geo);
   c.nrowc = lc.geo.nnodes;
   c.bl = band_layout(c.nrowc, c.bw);
+  c.bl.wait = (long long)h->opt.wait_cycles;
+  c.bl.stall = h->opt.inject_stall;
   assemble_band(lc.geo, lc.sc, lc.c2h, c.Kband, c.Mband, c.bw);
   c.Kb = h->upload(c.Kband);
   c.Mb = h->upload(c.Mband);
@@ -1552,10 +1558,24 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
     t.first[lev] = o;
   }
   for (int lev = jx_star; lev >= 0; --lev) t.first[lev] = std::min(t.first[lev], t.first[lev + 1]);
+  // The B-spline weights at the target times are dyadic rationals (target
+  // times and knots are both multiples of T / 2^max(jt, jt*)); with at most
+  // 24 significant bits they are exact floats, and the levels run in
+  // double-single arithmetic.  Otherwise (time levels more than 11 apart)
+  // every level runs in FP64.
+  std::vector<float> tbw(tb.size());
+  t.ds_ok = true;
+  for (size_t i = 0; i < tb.size(); ++i) {
+    tbw[i] = (float)tb[i];
+    if (std::fabs((double)tbw[i] - tb[i]) > 4e-16) t.ds_ok = false;
+  }
+  t.jt.resize(nc);
+  for (int o = 0; o < nc; ++o) t.jt[o] = cc[o].jt;
   t.comps = h->alloc<CombComp>(nc);
   t.tb = h->alloc<double>(tb.size());
+  t.tbw = h->alloc<float>(tbw.size());
   t.span = h->alloc<int>(tsp.size());
-  if (!t.comps || !t.tb || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
+  if (!t.comps || !t.tb || !t.tbw || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
   t.Y.assign(jx_star + 1, nullptr);
   for (int lev = t.jmin; lev < jx_star; ++lev) {
     int64_t nsp = 1;
@@ -1565,6 +1585,7 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
   }
   ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(h, cudaMemcpyAsync(t.tbw, tbw.data(), tbw.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
   *out = &(h->comb[key] = t);
@@ -1582,8 +1603,17 @@ void enqueue_comb_level(st_handle* h, const st_handle::CombTables& t, int lev, i
   int64_t nsp = 1;
   for (int k = 0; k < p.d; ++k) nsp *= ((1 << lev) + 1);
   const double outb = (double)nsp * nts * 8.0, inb = Yp ? outb / (1 << p.d) : 0.0;
-  PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, (double)nsp * nts * ((Yp ? 2.0 : 0.0) + 4.0 * (c1 - c0)),
-       launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
+  // algorithmic flops per target value: the prolongation's add and three
+  // multiply-adds per component
+  const double flops = (double)nsp * nts * ((Yp ? 1.0 : 0.0) + 6.0 * (c1 - c0));
+  if (t.ds_ok) {
+    const int L = comb_ds_chunk(p.d, lev, jt_star, t.jt.data() + c0, c1 - c0);
+    PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
+         launch_comb_level_ds(p.d, lev, Yp, t.comps, c0, c1, t.tbw, t.span, nts, L, Y, lev == jx_star, h->stream));
+  } else {
+    PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
+         launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
+  }
 }
 
 // Forward (S U = F) or adjoint (S^T L = G) solves of components k0..k1-1.
@@ -1714,6 +1744,8 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
     return fail(nullptr, ST_ERR_ARG, "tolerances must lie in [0, 1)");
   if (h->opt.max_direct_rows < 0) return fail(nullptr, ST_ERR_ARG, "max_direct_rows must be >= 0");
   if (h->opt.autotune < -1 || h->opt.autotune > 1) return fail(nullptr, ST_ERR_ARG, "autotune must be -1, 0 or 1");
+  if (h->opt.mem_cap_bytes < 0 || h->opt.wait_cycles < 0 || h->opt.inject_stall < 0 || h->opt.inject_stall > 1)
+    return fail(nullptr, ST_ERR_ARG, "mem_cap_bytes and wait_cycles must be >= 0, inject_stall 0 or 1");
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->nterm_rows = p.n_terms + 2;
   h->launches0 = kernel_launch_count();

@@ -17,8 +17,8 @@ def _stats(name, ms, gbytes, gflops, launches=1):
 
 
 def test_fp64_only_class_uses_fp64_peak_on_the_mixed_path():
-    # the combination computes in FP64 on both paths: 0.86 TFLOP/s is 69 % of 1.25, not of the FP32 rate
-    st = _stats("combine_level@1050625", 7.49, 10.77, 6.46)
+    # the refinement residual computes in FP64 on both paths: 0.86 TFLOP/s is 69 % of 1.25, not of the FP32 rate
+    st = _stats("st_residual_fp64@1050625", 7.49, 10.77, 6.46)
     r = bench.roofline(st, 6780.0, "measured", "fp32ir", ALU)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["peak"] == pytest.approx(1.25) and "FP64" in r["peak_source"]
@@ -81,7 +81,7 @@ def test_committed_traffic_file_parses():
 
 
 def test_alu_peak_comes_from_the_probe_figure():
-    st = _stats("combine_level@1050625", 7.49, 10.77, 6.46)
+    st = _stats("st_residual_fp64@1050625", 7.49, 10.77, 6.46)
     alu = {"fp64": (1000.0, "measured by st_probe_fma"), "fp32": (70000.0, "measured by st_probe_fma")}
     r = bench.roofline(st, 6780.0, "measured", "fp64", alu)
     assert r["peak"] == pytest.approx(1.0) and r["frac"] == pytest.approx(6.46 / 7.49, rel=1e-9)
@@ -93,3 +93,10 @@ def test_final_line_roofline_is_compact():
     r = bench.compact_roofline(bench.roofline(st, 6780.0, "measured", "fp64", ALU))
     assert set(r) == {"bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"}
     assert len(json.dumps(r)) < 200
+
+
+def test_combination_is_judged_against_hbm():
+    # double-single combination: FP32-pipe arithmetic, so the HBM fraction bounds it
+    st = _stats("combine_level@1050625", 2.0, 10.77, 7.5)
+    r = bench.roofline(st, 6780.0, "measured", "fp64", ALU)
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(10770.0 / 2.0 / 6780.0, rel=1e-9)
