@@ -106,6 +106,19 @@ typedef struct {
                            size) timed per grid size and mode count at setup,
                            before the COCG graphs are captured, and kept for the
                            process: 0 or 1 = on (default), -1 = the built-in rule */
+  int64_t mem_cap_bytes; /* device memory this handle may allocate in total
+                            (0 = no cap); an allocation beyond it fails with
+                            ST_ERR_OOM, as a real allocation failure would */
+  int64_t wait_cycles;  /* cycle budget of each bounded copy wait in the
+                           single-warp banded solves (grids with a half
+                           bandwidth above 128 that are not power-of-two
+                           bands): 0 = 2^31, about one second; a wait that runs
+                           out makes the solve return ST_ERR_TIMEOUT */
+  int inject_stall;     /* fault injection for failure tests: 1 = the first
+                           factor-row copy of every single-warp banded solve is
+                           never issued, so its bounded wait runs out after
+                           wait_cycles and the solve returns ST_ERR_TIMEOUT;
+                           0 = off (default) */
 } st_options;
 
 typedef struct {

@@ -246,7 +246,11 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
       cnt = min(C, nrow - k0);
       klo = pass == 0 ? k0 : nrow - k0 - cnt;
     };
+    // fault injection for the failure tests: the first copy is never issued,
+    // so its bounded wait runs out (nothing is left in flight for it)
+    const bool withhold0 = L.stall != 0 && pass == 0;
     auto issue = [&](int c) {
+      if (withhold0 && c == 0) return;
       int klo, cnt;
       chunk(c, klo, cnt);
       cx<R>* st = (c & 1) ? stage1 : stage0;
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
     for (int c = 0; c < nchunks; ++c) {
       // prefetch the right-hand sides entering during the next chunk
       const cx<R> pre = lane < C ? at((c + 1) * C + lane + bw) : zero;
-      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1]);
+      ok = mbar_wait_bounded(&bar[c & 1], phase[c & 1], L.wait > 0 ? L.wait : (1ll << 31));
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
@@ -344,7 +348,8 @@ __global__ void __launch_bounds__(32) k_band_solve_w(const cx<R>* __restrict__ F
       // give the copies still in flight a bounded chance to land, then report
       if (lane == 0) {
         atomicExch(err, 2);
-        for (int c2 = 0; c2 < 2; ++c2) mbar_wait_bounded(&bar[c2], phase[c2]);
+        for (int c2 = 0; c2 < 2; ++c2)
+          if (!(withhold0 && c2 == 0)) mbar_wait_bounded(&bar[c2], phase[c2]);
       }
       return;
     }
@@ -855,7 +860,7 @@ template <typename R> void set_smem_attr_ldlt(size_t bytes) {
 }  // namespace
 
 BandLayout band_layout(int64_t nrow, int bw) {
-  BandLayout L;
+  BandLayout L{};
   L.nrow = nrow;
   L.bw = bw;
   L.ld = (bw + 1 + 1) & ~1;

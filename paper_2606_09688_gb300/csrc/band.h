@@ -19,6 +19,9 @@ struct BandLayout {
   int bw;           // half bandwidth: 1 (1D), n+1 (2D), n^2+n+1 (3D)
   int ld;           // row length in elements: bw + 1 rounded up to even
   int64_t mstride;  // elements per mode (multiple of 32)
+  long long wait;   // cycle budget of the single-warp solve's copy waits (0 = 2^31)
+  int stall;        // fault injection (tests): the single-warp solve withholds its first copy
+  int pad;
 };
 
 BandLayout band_layout(int64_t nrow, int bw);

@@ -32,11 +32,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for a phase of the barrier for at most ~2^31 cycles (about one second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// Wait for a phase of the barrier for at most `budget` cycles (default 2^31,
+// about one second at 2 GHz); false if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long budget = (1ll << 31)) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }

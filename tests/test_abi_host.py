@@ -184,6 +184,11 @@ def test_setup_rejects_bad_solver_options_without_touching_the_gpu():
         assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
         assert msg in L.st_last_error(None)
         assert h.value is None
+    for cap, wait, stall in ((-1, 0, 0), (0, -5, 0), (0, 0, 2), (0, 0, -1)):
+        opt = B.StOptions(B.ST_FP64, 0.0, 0, 0, None, 0.0, 0, 0, cap, wait, stall)
+        assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
+        assert b"inject_stall" in L.st_last_error(None)
+        assert h.value is None
 
 
 def test_tuned_shape_pinning_validates_the_shape():
