@@ -18,7 +18,8 @@
 // node, with the lifting u0 folded in (the three B-splines of a span sum to
 // one), stay in registers as pairs, and each target value costs three pair
 // multiply-adds per component, the prolongation of its own share, and one
-// 8-byte store.  FP64 appears only in the per-chunk coefficient set-up.
+// 8-byte store.  The coefficients are converted to pairs once per step
+// (k_comb_prep_ds), so the level kernels run no FP64 instruction.
 #include "../../include/st_host.h"
 #include "dsfloat.h"
 #include "kernels.h"
@@ -30,9 +31,12 @@ constexpr int kCombThreads = 256;
 constexpr int kCombMaxChunk = 256;
 constexpr int kCombRegComps = 2;  // components held in registers per level
 
+// comps[c]: the component's coefficient pairs, the sign of its coefficient
+// applied and u0 folded in (U_ds[i][a] = coef (U[i][a] + u0(x_a))), and
+// coef u0 on all nodes of its level (null when u0 = 0), from k_comb_prep_ds.
 template <int D, int NR, bool FINAL>
-__global__ void __launch_bounds__(kCombThreads)
-    k_comb_ds(int j, const ds* __restrict__ Yprev, const CombComp* __restrict__ comps, int c0, int c1,
+__global__ void __launch_bounds__(kCombThreads, D == 3 ? 2 : 3)
+    k_comb_ds(int j, const ds* __restrict__ Yprev, const CombCompDS* __restrict__ comps, int c0, int c1,
               const float* __restrict__ tbw, const int* __restrict__ tspan, int nts, int L, ds* __restrict__ Yp,
               double* __restrict__ Yd, FastDiv dQ1) {
   constexpr int NE = 1 << D;
@@ -103,54 +107,47 @@ __global__ void __launch_bounds__(kCombThreads)
       st *= (Nc + 1);
     }
     cidx[e] = idx;
-    cok[e] = ok;
+    cok[e] = ok && Yprev != nullptr;
   }
-
-  // three time coefficients (u0 folded in, coefficient sign applied) of every
-  // owned node for each register-held component
+  // coefficient pair of owned node e in time row `row` of component cc (the
+  // lifting alone outside the interior and for the removed first B-spline)
+  auto coeff = [&](const CombCompDS& cc, int e, int row) -> ds {
+    const int sh = cc.jx - j;
+    const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
+    int64_t ii = 0, ia = 0, nx = 1, sa = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int P = (2 * Q[k] + ((e >> k) & 1)) << sh;
+      ii += (int64_t)(P - 1) * nx;
+      ia += (int64_t)P * sa;
+      nx *= n;
+      sa *= (N + 1);
+    }
+    if (interior[e] && row >= 0 && row < nt) return cc.U[(int64_t)row * nx + ii];
+    return (cc.lift != nullptr && inside[e]) ? cc.lift[ia] : ds{0.0f, 0.0f};
+  };
+  // three time coefficients of every owned node for each register-held component
   ds cf[NR > 0 ? NR : 1][NE][3];
   int cur[NR > 0 ? NR : 1];
 #pragma unroll
   for (int r = 0; r < NR; ++r) cur[r] = -1;
-  auto load_coeffs = [&](int r, int span) {
-    const CombComp cc = comps[c0 + r];
-    const int sh = cc.jx - j;
-    const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
-    int64_t nx = 1;
-#pragma unroll
-    for (int k = 0; k < D; ++k) nx *= n;
-#pragma unroll
-    for (int e = 0; e < NE; ++e) {
-      int64_t ii = 0, ia = 0, si = 1, sa = 1;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const int P = (2 * Q[k] + ((e >> k) & 1)) << sh;
-        ii += (int64_t)(P - 1) * si;
-        ia += (int64_t)P * sa;
-        si *= n;
-        sa *= (N + 1);
-      }
-      const double lift = (cc.lift != nullptr && inside[e]) ? cc.lift[ia] : 0.0;
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int row = span + t - 1;
-        double v = lift;
-        if (interior[e] && row >= 0 && row < nt) v += cc.U[(int64_t)row * nx + ii];
-        cf[r][e][t] = ds_from_double(cc.coef > 0 ? v : -v);
-      }
-    }
-  };
 
+  // level j-1 values at the chunk's first time; the next time's are loaded
+  // one step ahead
+  ds fn[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) fn[e] = cok[e] ? Yprev[(int64_t)s0 * ncs + cidx[e]] : ds{0.0f, 0.0f};
   for (int s = s0; s < s1; ++s) {
-    // prolongation of level j-1 (zero at the coarsest level)
     ds f[NE];
 #pragma unroll
-    for (int e = 0; e < NE; ++e) f[e] = ds{0.0f, 0.0f};
-    if (Yprev != nullptr) {
-      const ds* Ys = Yprev + (int64_t)s * ncs;
+    for (int e = 0; e < NE; ++e) f[e] = fn[e];
+    if (s + 1 < s1) {
 #pragma unroll
       for (int e = 0; e < NE; ++e)
-        if (cok[e]) f[e] = Ys[cidx[e]];
+        if (cok[e]) fn[e] = Yprev[(int64_t)(s + 1) * ncs + cidx[e]];
+    }
+    // prolongation: midpoints averaged direction by direction
+    if (Yprev != nullptr) {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
 #pragma unroll
@@ -168,7 +165,11 @@ __global__ void __launch_bounds__(kCombThreads)
     for (int r = 0; r < NR; ++r) {
       const int sp = ssp[r][s - s0];
       if (sp != cur[r]) {
-        load_coeffs(r, sp);
+        const CombCompDS cc = comps[c0 + r];
+#pragma unroll
+        for (int e = 0; e < NE; ++e)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) cf[r][e][t] = coeff(cc, e, sp + t - 1);
         cur[r] = sp;
       }
       const float w0 = sw[r][s - s0][0], w1 = sw[r][s - s0][1], w2 = sw[r][s - s0][2];
@@ -180,37 +181,14 @@ __global__ void __launch_bounds__(kCombThreads)
       }
     }
     // components beyond the register-held ones (several components injected
-    // into the target level): FP64 evaluation per value, then added as a pair
+    // into the target level): coefficients read at every time
     for (int c = c0 + NR; c < c1; ++c) {
-      const CombComp cc = comps[c];
-      const int sh = cc.jx - j;
-      const int N = 1 << cc.jx, n = N - 1, nt = (1 << cc.jt) + 1;
+      const CombCompDS cc = comps[c];
       const int span = tspan[(int64_t)c * nts + s];
       const float* w = tbw + ((int64_t)c * nts + s) * 3;
-      int64_t nx = 1;
-      for (int k = 0; k < D; ++k) nx *= n;
 #pragma unroll
-      for (int e = 0; e < NE; ++e) {
-        if (!inside[e]) continue;
-        int64_t ii = 0, ia = 0, si = 1, sa = 1;
-        for (int k = 0; k < D; ++k) {
-          const int P = (2 * Q[k] + ((e >> k) & 1)) << sh;
-          ii += (int64_t)(P - 1) * si;
-          ia += (int64_t)P * sa;
-          si *= n;
-          sa *= (N + 1);
-        }
-        double v = cc.lift != nullptr ? cc.lift[ia] : 0.0;
-        if (interior[e])
-          for (int t = 0; t < 3; ++t) {
-            const int row = span + t - 1;
-            if (row >= 0 && row < nt) v = fma((double)w[t], cc.U[(int64_t)row * nx + ii], v);
-          }
-        const ds a = ds_from_double(cc.coef > 0 ? v : -v);
-        float se;
-        two_sum(S[e], a.h, S[e], se);
-        lo[e] = f_add(lo[e], f_add(se, a.l));
-      }
+      for (int e = 0; e < NE; ++e)
+        for (int t = 0; t < 3; ++t) ds_axpy(w[t], coeff(cc, e, span + t - 1), S[e], lo[e]);
     }
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
@@ -222,8 +200,41 @@ __global__ void __launch_bounds__(kCombThreads)
   }
 }
 
+// Pairs of one component for the level kernels: Uds[i][a] = coef (U[i][a] +
+// u0(x_a)) on the interior nodes, Lds[b] = coef u0(x_b) on all nodes.
+template <int D>
+__global__ void __launch_bounds__(kCombThreads)
+    k_comb_prep_ds(const double* __restrict__ U, const double* __restrict__ lift, int coef, int jx, int nt,
+                   ds* __restrict__ Uds, ds* __restrict__ Lds) {
+  const int N = 1 << jx, n = N - 1;
+  int64_t nx = 1, na = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    nx *= n;
+    na *= (N + 1);
+  }
+  const int64_t e = (int64_t)blockIdx.x * kCombThreads + threadIdx.x;
+  if (e < nt * nx) {
+    double v = U[e];
+    if (lift != nullptr) {
+      unsigned r = (unsigned)(e % nx);  // interior node (fewer than 2^31 per level)
+      int64_t ia = 0, sa = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const unsigned q = r / (unsigned)n;
+        ia += (int64_t)(r - q * (unsigned)n + 1) * sa;
+        r = q;
+        sa *= (N + 1);
+      }
+      v += lift[ia];
+    }
+    Uds[e] = ds_from_double(coef > 0 ? v : -v);
+  }
+  if (lift != nullptr && e < na) Lds[e] = ds_from_double(coef > 0 ? lift[e] : -lift[e]);
+}
+
 template <int D, int NR>
-void launch_ds(bool final_level, dim3 grid, int j, const ds* Yprev, const CombComp* comps, int c0, int c1,
+void launch_ds(bool final_level, dim3 grid, int j, const ds* Yprev, const CombCompDS* comps, int c0, int c1,
                const float* tbw, const int* tspan, int nts, int L, ds* Yp, double* Yd, FastDiv f, cudaStream_t s) {
   if (final_level)
     k_comb_ds<D, NR, true><<<grid, kCombThreads, 0, s>>>(j, Yprev, comps, c0, c1, tbw, tspan, nts, L, Yp, Yd, f);
@@ -232,8 +243,8 @@ void launch_ds(bool final_level, dim3 grid, int j, const ds* Yprev, const CombCo
 }
 
 template <int D>
-void launch_ds_d(int nr, bool final_level, dim3 grid, int j, const ds* Yprev, const CombComp* comps, int c0, int c1,
-                 const float* tbw, const int* tspan, int nts, int L, ds* Yp, double* Yd, FastDiv f,
+void launch_ds_d(int nr, bool final_level, dim3 grid, int j, const ds* Yprev, const CombCompDS* comps, int c0,
+                 int c1, const float* tbw, const int* tspan, int nts, int L, ds* Yp, double* Yd, FastDiv f,
                  cudaStream_t s) {
   if (nr == 0) launch_ds<D, 0>(final_level, grid, j, Yprev, comps, c0, c1, tbw, tspan, nts, L, Yp, Yd, f, s);
   else if (nr == 1) launch_ds<D, 1>(final_level, grid, j, Yprev, comps, c0, c1, tbw, tspan, nts, L, Yp, Yd, f, s);
@@ -259,7 +270,22 @@ int comb_ds_chunk(int d, int j, int jt_star, const int* comp_jt, int ncomp_level
   return L < 1 ? 1 : L;
 }
 
-void launch_comb_level_ds(int d, int j, const void* Yprev, const CombComp* comps, int c0, int c1, const float* tbw,
+void launch_comb_prep_ds(int d, const double* U, const double* lift, int coef, int jx, int nt, ds* Uds, ds* Lds,
+                         cudaStream_t s) {
+  note_launches(1);
+  int64_t nx = 1, na = 1;
+  for (int k = 0; k < d; ++k) {
+    nx *= (1 << jx) - 1;
+    na *= (1 << jx) + 1;
+  }
+  const int64_t n = nt * nx > na ? nt * nx : na;
+  const unsigned blocks = (unsigned)((n + kCombThreads - 1) / kCombThreads);
+  if (d == 1) k_comb_prep_ds<1><<<blocks, kCombThreads, 0, s>>>(U, lift, coef, jx, nt, Uds, Lds);
+  else if (d == 2) k_comb_prep_ds<2><<<blocks, kCombThreads, 0, s>>>(U, lift, coef, jx, nt, Uds, Lds);
+  else k_comb_prep_ds<3><<<blocks, kCombThreads, 0, s>>>(U, lift, coef, jx, nt, Uds, Lds);
+}
+
+void launch_comb_level_ds(int d, int j, const void* Yprev, const CombCompDS* comps, int c0, int c1, const float* tbw,
                           const int* tspan, int nts, int L, void* Y, bool final_level, cudaStream_t s) {
   note_launches(1);
   int64_t ncs = 1;  // one thread per node of level j-1 (each writes up to 2^d level-j nodes)

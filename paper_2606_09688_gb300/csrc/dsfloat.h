@@ -128,30 +128,29 @@ __host__ __device__ __forceinline__ double ll_bits_d(uint64_t u) {
 
 // The double nearest (to within one unit in its last place) to h + l for a
 // renormalised pair (|l| <= half an ulp of h), formed with integer and float
-// operations only: the exact double of h (its exponent re-biased, its
+// operations only: the exact double of |h| (its exponent re-biased, its
 // significand shifted into place), plus l counted in units of the last place
-// of that double, k = round(l 2^(52 - e_h)), |k| <= 2^28.  When h is a power of
-// two and l points towards zero, the result lies in the binade below, whose
-// unit is half as large, so k is counted in those units.  h = 0 or subnormal
-// gives 0; infinities and NaN pass through.
+// of that double, k = round(l sign(h) 2^(52 - e_h)), |k| <= 2^28, then h's sign.
+// When h is a power of two and l points towards zero, the result lies in the
+// binade below, whose unit is half as large, so k is doubled.  For
+// |h| < 2^-74 the scale 2^(52 - e) is beyond the float range and is applied in
+// two factors (2^64 first).  h = 0 or subnormal gives a signed zero;
+// infinities and NaN give NaN.
 __host__ __device__ __forceinline__ double ds_to_double(ds x) {
   const uint32_t hb = f_bits(x.h);
-  const uint32_t e8 = (hb >> 23) & 0xffu;
-  if (e8 == 0u) return 0.0;
-  if (e8 == 0xffu) return (double)x.h;
-  const uint32_t hw = (hb & 0x80000000u) | (((hb & 0x7fffffffu) >> 3) + 0x38000000u);
-  const uint32_t lw = hb << 29;
-  // 2^(52 - e) with e = e8 - 127, as a float: exponent field 306 - e8 when
-  // e8 >= 53; below that the product is taken in two steps (2^64 first)
+  const uint32_t sgn = hb & 0x80000000u;
+  const uint32_t mag = hb & 0x7fffffffu;
+  const uint32_t e8 = mag >> 23;
+  if (e8 == 0u || e8 == 0xffu) return ll_bits_d(((uint64_t)sgn << 32) | (e8 == 0u ? 0ull : 0x7ff8000000000000ull));
+  const uint32_t hw = (mag >> 3) + 0x38000000u;
+  const uint32_t lw = mag << 29;
   const bool small = e8 < 53u;
-  const float sc = bits_f((small ? (242u - e8) : (306u - e8)) << 23);
-  float t = small ? f_mul(x.l, 18446744073709551616.0f) : x.l;
-  // l pointing towards zero from a power of two: units of the binade below
-  const bool down = ((hb & 0x007fffffu) == 0u) && (((f_bits(x.l) ^ hb) & 0x80000000u) != 0u) && x.l != 0.0f;
-  t = f_mul(t, down ? f_mul(sc, 2.0f) : sc);
-  int k = f2i_rn(t);
-  if (hb & 0x80000000u) k = -k;
-  const uint64_t r = (((uint64_t)hw << 32) | (uint64_t)lw) + (uint64_t)(int64_t)k;
+  const uint32_t fe = small ? 242u - e8 : 306u - e8;  // float exponent field of 2^(52 - e) (/ 2^64 if small)
+  float lm = bits_f(f_bits(x.l) ^ sgn);               // l relative to the sign of h
+  if (small) lm = f_mul(lm, 18446744073709551616.0f);
+  int k = f2i_rn(f_mul(lm, bits_f(fe << 23)));
+  if ((mag & 0x007fffffu) == 0u && k < 0) k *= 2;
+  const uint64_t r = ((((uint64_t)hw << 32) | (uint64_t)lw) + (uint64_t)(int64_t)k) | ((uint64_t)sgn << 32);
   return ll_bits_d(r);
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dsfloat.h"
 
 namespace st {
 
@@ -93,11 +94,20 @@ void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps,
                        const int* tspan, int nts, double* Y, cudaStream_t s);
 // The same level in double-single arithmetic (combine_ds.cu): Yprev and, below
 // the target level, Y hold float pairs (8 bytes per value); the target level
-// (final_level) is written as FP64.  tbw: the B-spline weights as floats,
-// exact (the caller checks that every weight is representable).  L: target
-// times per chunk, from comb_ds_chunk (comp_jt: time levels of the level's
-// components, in table order).
-void launch_comb_level_ds(int d, int j, const void* Yprev, const CombComp* comps, int c0, int c1, const float* tbw,
+// (final_level) is written as FP64.  comps: per component its coefficient
+// pairs with the coefficient's sign applied and u0 folded in, and coef u0 on
+// all nodes of its level (from launch_comb_prep_ds).  tbw: the B-spline
+// weights as floats, exact (the caller checks that every weight is
+// representable).  L: target times per chunk, from comb_ds_chunk (comp_jt:
+// time levels of the level's components, in table order).
+struct CombCompDS {
+  const ds* U;     // nt x nx interior pairs: coef (U + u0)
+  const ds* lift;  // coef u0 on all nodes of level jx, or nullptr
+  int jx, jt;
+};
+void launch_comb_prep_ds(int d, const double* U, const double* lift, int coef, int jx, int nt, ds* Uds, ds* Lds,
+                         cudaStream_t s);
+void launch_comb_level_ds(int d, int j, const void* Yprev, const CombCompDS* comps, int c0, int c1, const float* tbw,
                           const int* tspan, int nts, int L, void* Y, bool final_level, cudaStream_t s);
 int comb_ds_chunk(int d, int j, int jt_star, const int* comp_jt, int ncomp_level);
 

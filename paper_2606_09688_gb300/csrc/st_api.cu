@@ -192,6 +192,8 @@ struct Component {
   double* KU = nullptr;
   double* MU = nullptr;
   double* Fg_all = nullptr;  // general source, time-projected on all nodes (nt x nall), or nullptr
+  ds* Uds = nullptr;         // coef (U + u0) as pairs for the combination (nt x nx), on first use
+  ds* Lds = nullptr;         // coef u0 on all nodes as pairs, or nullptr
   bool f_ready = false;
   bool solved = false;
   // time eigenbasis
@@ -275,6 +277,7 @@ struct st_handle {
     CombComp* comps = nullptr;  // components ordered by combination level
     double* tb = nullptr;
     float* tbw = nullptr;       // the same weights as floats (exact when ds_ok)
+    CombCompDS* dcomps = nullptr;  // the components' pair arrays, table order
     bool ds_ok = false;         // every weight exact in FP32: double-single levels
     std::vector<int> jt;        // time level of each table entry
     int* span = nullptr;
@@ -1571,11 +1574,25 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
   }
   t.jt.resize(nc);
   for (int o = 0; o < nc; ++o) t.jt[o] = cc[o].jt;
+  // pair arrays of every component (kept on the component, filled per step)
+  std::vector<CombCompDS> dc(nc);
+  if (t.ds_ok)
+    for (int o = 0; o < nc; ++o) {
+      Component& k = *h->comps[order[o]];
+      if (k.Uds == nullptr) {
+        k.Uds = h->alloc<ds>((size_t)k.nt * k.nx);
+        if (k.sl->lift != nullptr) k.Lds = h->alloc<ds>((size_t)k.sl->nall);
+        if (k.Uds == nullptr || (k.sl->lift != nullptr && k.Lds == nullptr))
+          return fail(h, ST_ERR_OOM, "device allocation failed");
+      }
+      dc[o] = CombCompDS{k.Uds, k.Lds, k.jx, k.jt};
+    }
   t.comps = h->alloc<CombComp>(nc);
   t.tb = h->alloc<double>(tb.size());
   t.tbw = h->alloc<float>(tbw.size());
+  t.dcomps = h->alloc<CombCompDS>(nc);
   t.span = h->alloc<int>(tsp.size());
-  if (!t.comps || !t.tb || !t.tbw || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
+  if (!t.comps || !t.tb || !t.tbw || !t.dcomps || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
   t.Y.assign(jx_star + 1, nullptr);
   for (int lev = t.jmin; lev < jx_star; ++lev) {
     int64_t nsp = 1;
@@ -1586,6 +1603,7 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
   ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.tbw, tbw.data(), tbw.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(h, cudaMemcpyAsync(t.dcomps, dc.data(), nc * sizeof(CombCompDS), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
   *out = &(h->comb[key] = t);
@@ -1607,9 +1625,14 @@ void enqueue_comb_level(st_handle* h, const st_handle::CombTables& t, int lev, i
   // multiply-adds per component
   const double flops = (double)nsp * nts * ((Yp ? 1.0 : 0.0) + 6.0 * (c1 - c0));
   if (t.ds_ok) {
+    // this level's components as pairs (sign applied, u0 folded in), then the level
+    for (int o = c0; o < c1; ++o) {
+      const Component& k = *h->comps[t.order[o]];
+      launch_comb_prep_ds(p.d, k.U, k.sl->lift, k.coef, k.jx, k.nt, k.Uds, k.Lds, h->stream);
+    }
     const int L = comb_ds_chunk(p.d, lev, jt_star, t.jt.data() + c0, c1 - c0);
     PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
-         launch_comb_level_ds(p.d, lev, Yp, t.comps, c0, c1, t.tbw, t.span, nts, L, Y, lev == jx_star, h->stream));
+         launch_comb_level_ds(p.d, lev, Yp, t.dcomps, c0, c1, t.tbw, t.span, nts, L, Y, lev == jx_star, h->stream));
   } else {
     PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
          launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
