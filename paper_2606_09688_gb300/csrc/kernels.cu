@@ -868,27 +868,68 @@ __global__ void k_gemm_right(const double* __restrict__ X, const double* __restr
 
 // Banded LU solve with partial pivoting (factor layout of band_lu, spatial
 // mode fastest), one thread per spatial mode, Y column a (stride nx) in place.
-__global__ void k_time_band_solve(const double* __restrict__ ab, const int* __restrict__ piv, double* __restrict__ Y,
-                                  int nt, int64_t nx, int kl, int ku) {
-  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nx) return;
-  const int kv = kl + ku, ld = 2 * kl + ku + 1;
-  auto A = [&](int i, int j) -> double { return ab[((int64_t)(kv + i - j) + (int64_t)j * ld) * nx + a]; };
-  for (int j = 0; j < nt; ++j) {
-    const int p = piv[(int64_t)j * nx + a];
-    double yj = Y[(int64_t)p * nx + a];
-    if (p != j) {
-      Y[(int64_t)p * nx + a] = Y[(int64_t)j * nx + a];
-      Y[(int64_t)j * nx + a] = yj;
+// Banded LU solves (A + mu_a B) y_a = r_a, one spatial mode a per CTA: the
+// mode's factor (mode-major: column j of the band at j * ld, the diagonal
+// stored as its reciprocal), pivots and right-hand side are staged in shared
+// memory, then one thread runs the forward (row interchanges, unit lower
+// factor, kl sub-diagonals) and backward (upper factor, kl + ku
+// super-diagonals) recurrences on a register window of the rows in reach, so
+// each step waits on two shared-memory loads and its own multiply-adds.
+template <int KL, int KU>
+__global__ void __launch_bounds__(128) k_time_band_solve(const double* __restrict__ ab, const int* __restrict__ piv,
+                                                         double* __restrict__ Y, int nt, int64_t nx) {
+  constexpr int KV = KL + KU, LD = 2 * KL + KU + 1;
+  extern __shared__ __align__(16) unsigned char tb_smem[];
+  double* sa = reinterpret_cast<double*>(tb_smem);  // nt x LD
+  double* sy = sa + (size_t)nt * LD;                // nt
+  int* sp = reinterpret_cast<int*>(sy + nt);        // nt
+  const int64_t a = blockIdx.x;
+  const double* aba = ab + a * (int64_t)nt * LD;
+  for (int e = threadIdx.x; e < nt * LD; e += blockDim.x) sa[e] = aba[e];
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+    sp[j] = piv[a * nt + j];
+    sy[j] = Y[(int64_t)j * nx + a];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // forward: window w[0..KL] = rows j .. j+KL
+    double w[KL + 1];
+#pragma unroll
+    for (int t = 0; t <= KL; ++t) w[t] = t < nt ? sy[t] : 0.0;
+    for (int j = 0; j < nt; ++j) {
+      const int p = sp[j] - j;  // 0 .. KL
+      double yj = w[0];
+#pragma unroll
+      for (int t = 1; t <= KL; ++t) {
+        const double wt = w[t];
+        w[t] = (p == t) ? yj : wt;
+        yj = (p == t) ? wt : yj;
+      }
+      const double* col = sa + (size_t)j * LD + KV;  // col[i - j] = A(i, j)
+#pragma unroll
+      for (int t = 1; t <= KL; ++t) w[t] = (j + t < nt) ? fma(-col[t], yj, w[t]) : w[t];
+      sy[j] = yj;
+#pragma unroll
+      for (int t = 0; t < KL; ++t) w[t] = w[t + 1];
+      w[KL] = (j + KL + 1 < nt) ? sy[j + KL + 1] : 0.0;
     }
-    const int km = min(kl, nt - 1 - j);
-    for (int i = j + 1; i <= j + km; ++i) Y[(int64_t)i * nx + a] -= A(i, j) * yj;
+    // backward: window w[0..KV] = rows j, j-1, .., j-KV
+    double v[KV + 1];
+#pragma unroll
+    for (int t = 0; t <= KV; ++t) v[t] = (nt - 1 - t >= 0) ? sy[nt - 1 - t] : 0.0;
+    for (int j = nt - 1; j >= 0; --j) {
+      const double* col = sa + (size_t)j * LD + KV;  // col[i - j] = A(i, j), col[0] = 1 / A(j, j)
+      const double yj = v[0] * col[0];
+      sy[j] = yj;
+#pragma unroll
+      for (int t = 1; t <= KV; ++t) v[t] = (j - t >= 0) ? fma(-col[-t], yj, v[t]) : v[t];
+#pragma unroll
+      for (int t = 0; t < KV; ++t) v[t] = v[t + 1];
+      v[KV] = (j - KV - 1 >= 0) ? sy[j - KV - 1] : 0.0;
+    }
   }
-  for (int j = nt - 1; j >= 0; --j) {
-    const double yj = Y[(int64_t)j * nx + a] / A(j, j);
-    Y[(int64_t)j * nx + a] = yj;
-    for (int i = max(0, j - kv); i < j; ++i) Y[(int64_t)i * nx + a] -= A(i, j) * yj;
-  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) Y[(int64_t)j * nx + a] = sy[j];
 }
 
 // --------------------------------------------------------------- combination
@@ -1432,10 +1473,16 @@ void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, in
   k_gemm_right<<<grid, block, 0, s>>>(X, Phi, Y, nt, nx, accumulate);
 }
 
-void launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
+size_t time_band_smem(int nt) { return (size_t)nt * (7 * sizeof(double) + sizeof(double) + sizeof(int)); }
+
+bool launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
                             cudaStream_t s) {
+  if (kl != 2 || ku != 2 || time_band_smem(nt) > kTimeBandMaxSmem) return false;
   count(1);
-  k_time_band_solve<<<blocks_for(nx, 128), 128, 0, s>>>(ab, piv, Y, nt, nx, kl, ku);
+  // set for the current device at every launch (a host-side attribute call)
+  cudaFuncSetAttribute(k_time_band_solve<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTimeBandMaxSmem);
+  k_time_band_solve<2, 2><<<(unsigned)nx, 128, time_band_smem(nt), s>>>(ab, piv, Y, nt, nx);
+  return true;
 }
 
 void launch_comb_level(int d, int j, const double* Yprev, const CombComp* comps, int c0, int c1, const double* tbv,

@@ -76,7 +76,14 @@ void launch_rhs_assemble(const double* coef, const double* L, double* F, int nte
 // X nt x nx, Phi nx x nx; then banded time solves per spatial mode.
 void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, int64_t nx, int trans, int accumulate,
                        cudaStream_t s);
-void launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
+// Band LU factors per spatial mode a: ab[a][j][0..6] = column j of the band
+// (LAPACK band layout, kl = ku = 2, row i of column j at 4 + i - j), the
+// diagonal entry replaced by its reciprocal; piv[a][j].  Returns false (and
+// launches nothing) when the mode's factor does not fit in shared memory
+// (time_band_smem(nt) > kTimeBandMaxSmem) or the bandwidths differ.
+constexpr size_t kTimeBandMaxSmem = 200 * 1024;
+size_t time_band_smem(int nt);
+bool launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,
                             cudaStream_t s);
 
 // Combination kernel (Eq. (19)) on a nodal target grid.

@@ -784,6 +784,8 @@ st_status setup_component(st_handle* h, Component& c) {
     ST_NEED(h, c.Phi);
     ST_NEED(h, c.PhiT);
     const int nt = c.nt, kl = 2, ku = 2, ld = 2 * kl + ku + 1;
+    if (time_band_smem(nt) > kTimeBandMaxSmem)
+      return fail(h, ST_ERR_ARG, "time level too fine for the space-eigenbasis band solve");
     // LU of A + mu_a B (forward) and of its transpose (adjoint) per spatial mode
     for (int tr = 0; tr < 2; ++tr) {
       std::vector<double> abAll((size_t)ld * nt * nx, 0.0);
@@ -798,8 +800,10 @@ st_status setup_component(st_handle* h, Component& c) {
             ab[(size_t)(kl + ku + i - j) + (size_t)j * ld] = c.td->tl.A[e] + mu[a] * c.td->tl.B[e];
           }
         if (!band_lu(nt, kl, ku, ab, piv)) return fail(h, ST_ERR_NUMERIC, "time band LU failed");
-        for (size_t e = 0; e < ab.size(); ++e) abAll[e * nx + a] = ab[e];
-        for (int j = 0; j < nt; ++j) pivAll[(size_t)j * nx + a] = piv[j];
+        // mode-major for the solve kernel, the diagonal of U as its reciprocal
+        for (int j = 0; j < nt; ++j) ab[(size_t)(kl + ku) + (size_t)j * ld] = 1.0 / ab[(size_t)(kl + ku) + (size_t)j * ld];
+        std::copy(ab.begin(), ab.end(), abAll.begin() + (size_t)a * ld * nt);
+        std::copy(piv.begin(), piv.end(), pivAll.begin() + (size_t)a * nt);
       }
       double* abd = h->upload(abAll);
       int* pivd = h->upload(pivAll);
@@ -1313,8 +1317,10 @@ st_status sweep_space_eig(st_handle* h, Component& c, const SolveIO& io, const d
   const double nx = (double)c.nx, nt = c.nt;
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
        launch_gemm_right(Rin, c.Phi, c.KU, c.nt, c.nx, 0, 0, c.cs));
+  bool ok = true;
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (2.0 * nt * nx + 7.0 * nt * nx) * 8.0, 12.0 * nt * nx,
-       launch_time_band_solve(io.lu_ab, io.lu_piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
+       ok = launch_time_band_solve(io.lu_ab, io.lu_piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs));
+  if (!ok) return cfail(c, ST_ERR_ARG, "time band solve: unsupported size");
   PROF(h, c.cs, KC_SPACE_EIG, (int64_t)(c.nx), (3.0 * nt * nx + nx * nx) * 8.0, 2.0 * nt * nx * nx,
        launch_gemm_right(c.KU, c.PhiT, io.sol, c.nt, c.nx, 1, 1, c.cs));
   return ccheck(c, "space eigenbasis sweep");

@@ -26,7 +26,6 @@ from oracle import combination, solve as osolve  # noqa: E402
 FIXTURES = {
     "layered_2d_n12_m2": (lambda: W.layered_2d(12, 2), (10, 10), 64, 16, 1201),
     "random_medium_3d_n8_m3": (lambda: W.random_medium_3d(8, 3), (5, 5), 64, 16, 803),
-    "random_medium_3d_n9_m3": (lambda: W.random_medium_3d(9, 3), (6, 6), 64, 16, 903),
 }
 
 
