@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(kCombThreads, D == 3 ? 2 : 3)
 }
 
 // Pairs of one component for the level kernels: Uds[i][a] = coef (U[i][a] +
-// u0(x_a)) on the interior nodes, Lds[b] = coef u0(x_b) on all nodes.
+// u0(x_a)) on the interior nodes, Lds[b] = coef u0(x_b) on all nodes (either
+// output may be null and is then skipped).
 template <int D>
 __global__ void __launch_bounds__(kCombThreads)
     k_comb_prep_ds(const double* __restrict__ U, const double* __restrict__ lift, int coef, int jx, int nt,
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kCombThreads)
     na *= (N + 1);
   }
   const int64_t e = (int64_t)blockIdx.x * kCombThreads + threadIdx.x;
-  if (e < nt * nx) {
+  if (Uds != nullptr && e < nt * nx) {
     double v = U[e];
     if (lift != nullptr) {
       unsigned r = (unsigned)(e % nx);  // interior node (fewer than 2^31 per level)
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kCombThreads)
     }
     Uds[e] = ds_from_double(coef > 0 ? v : -v);
   }
-  if (lift != nullptr && e < na) Lds[e] = ds_from_double(coef > 0 ? lift[e] : -lift[e]);
+  if (Lds != nullptr && lift != nullptr && e < na) Lds[e] = ds_from_double(coef > 0 ? lift[e] : -lift[e]);
 }
 
 template <int D, int NR>
@@ -278,7 +279,7 @@ void launch_comb_prep_ds(int d, const double* U, const double* lift, int coef, i
     nx *= (1 << jx) - 1;
     na *= (1 << jx) + 1;
   }
-  const int64_t n = nt * nx > na ? nt * nx : na;
+  const int64_t n = (Uds != nullptr && nt * nx > na) ? nt * nx : (Lds != nullptr ? na : nt * nx);
   const unsigned blocks = (unsigned)((n + kCombThreads - 1) / kCombThreads);
   if (d == 1) k_comb_prep_ds<1><<<blocks, kCombThreads, 0, s>>>(U, lift, coef, jx, nt, Uds, Lds);
   else if (d == 2) k_comb_prep_ds<2><<<blocks, kCombThreads, 0, s>>>(U, lift, coef, jx, nt, Uds, Lds);

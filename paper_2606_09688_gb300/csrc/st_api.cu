@@ -192,8 +192,8 @@ struct Component {
   double* KU = nullptr;
   double* MU = nullptr;
   double* Fg_all = nullptr;  // general source, time-projected on all nodes (nt x nall), or nullptr
-  ds* Uds = nullptr;         // coef (U + u0) as pairs for the combination (nt x nx), on first use
-  ds* Lds = nullptr;         // coef u0 on all nodes as pairs, or nullptr
+  ds* Uds[2] = {nullptr, nullptr};  // coef (U + u0) as pairs for the combination (nt x nx), two buffers
+  ds* Lds = nullptr;                 // coef u0 on all nodes as pairs, or nullptr (written once)
   bool f_ready = false;
   bool solved = false;
   // time eigenbasis
@@ -273,11 +273,21 @@ struct st_handle {
   int* dev_err = nullptr;
   int* solve_err = nullptr;  // set by bounded waits inside the band solve
   cudaEvent_t entry_ev = nullptr;
+  // Back-to-back st_solve_combine calls overlap (st_solve_combine): api_seq
+  // counts the calls that may enqueue work on the handle's stream, sc_seq is
+  // the count at the last st_solve_combine, sc_parity the pair buffer its
+  // successor uses, sc_done_ev[p] the end of the levels of the last call that
+  // used buffer p.
+  int64_t api_seq = 0;
+  int64_t sc_seq = -1;
+  int sc_parity = 0;
+  cudaEvent_t sc_done_ev[2] = {nullptr, nullptr};
+  bool sc_done_rec[2] = {false, false};
   struct CombTables {
     CombComp* comps = nullptr;  // components ordered by combination level
     double* tb = nullptr;
     float* tbw = nullptr;       // the same weights as floats (exact when ds_ok)
-    CombCompDS* dcomps = nullptr;  // the components' pair arrays, table order
+    CombCompDS* dcomps[2] = {nullptr, nullptr};  // the components' pair arrays (two buffers), table order
     bool ds_ok = false;         // every weight exact in FP32: double-single levels
     std::vector<int> jt;        // time level of each table entry
     int* span = nullptr;
@@ -336,6 +346,8 @@ struct st_handle {
       if (c->done) cudaEventDestroy(c->done);
     }
     if (entry_ev) cudaEventDestroy(entry_ev);
+    for (auto e : sc_done_ev)
+      if (e) cudaEventDestroy(e);
     for (auto& r : prof) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
@@ -1392,7 +1404,12 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
 // Execution context of a component: stream, completion event, reduction
 // scratch, and its workspace prepared for the handle's precision.
 st_status setup_context(st_handle* h, Component& c) {
-  ST_CUDA(h, cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking));
+  // the solves run at the highest stream priority: when a step's solves
+  // overlap the previous step's combination levels (st_solve_combine), their
+  // CTAs are placed first as the level kernels' CTAs drain
+  int prio_lo = 0, prio_hi = 0;
+  ST_CUDA(h, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  ST_CUDA(h, cudaStreamCreateWithPriority(&c.cs, cudaStreamNonBlocking, prio_hi));
   ST_CUDA(h, cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
   c.cpart = h->alloc<double>(304);
   c.cscalar = h->alloc<double>(1);
@@ -1581,24 +1598,31 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
   t.jt.resize(nc);
   for (int o = 0; o < nc; ++o) t.jt[o] = cc[o].jt;
   // pair arrays of every component (kept on the component, filled per step)
-  std::vector<CombCompDS> dc(nc);
+  std::vector<CombCompDS> dc[2];
+  dc[0].resize(nc);
+  dc[1].resize(nc);
   if (t.ds_ok)
     for (int o = 0; o < nc; ++o) {
       Component& k = *h->comps[order[o]];
-      if (k.Uds == nullptr) {
-        k.Uds = h->alloc<ds>((size_t)k.nt * k.nx);
+      if (k.Uds[0] == nullptr) {
+        k.Uds[0] = h->alloc<ds>((size_t)k.nt * k.nx);
+        k.Uds[1] = h->alloc<ds>((size_t)k.nt * k.nx);
         if (k.sl->lift != nullptr) k.Lds = h->alloc<ds>((size_t)k.sl->nall);
-        if (k.Uds == nullptr || (k.sl->lift != nullptr && k.Lds == nullptr))
+        if (k.Uds[0] == nullptr || k.Uds[1] == nullptr || (k.sl->lift != nullptr && k.Lds == nullptr))
           return fail(h, ST_ERR_OOM, "device allocation failed");
+        if (k.Lds != nullptr)
+          launch_comb_prep_ds(p.d, nullptr, k.sl->lift, k.coef, k.jx, k.nt, nullptr, k.Lds, h->stream);
       }
-      dc[o] = CombCompDS{k.Uds, k.Lds, k.jx, k.jt};
+      for (int b = 0; b < 2; ++b) dc[b][o] = CombCompDS{k.Uds[b], k.Lds, k.jx, k.jt};
     }
   t.comps = h->alloc<CombComp>(nc);
   t.tb = h->alloc<double>(tb.size());
   t.tbw = h->alloc<float>(tbw.size());
-  t.dcomps = h->alloc<CombCompDS>(nc);
+  t.dcomps[0] = h->alloc<CombCompDS>(nc);
+  t.dcomps[1] = h->alloc<CombCompDS>(nc);
   t.span = h->alloc<int>(tsp.size());
-  if (!t.comps || !t.tb || !t.tbw || !t.dcomps || !t.span) return fail(h, ST_ERR_OOM, "device allocation failed");
+  if (!t.comps || !t.tb || !t.tbw || !t.dcomps[0] || !t.dcomps[1] || !t.span)
+    return fail(h, ST_ERR_OOM, "device allocation failed");
   t.Y.assign(jx_star + 1, nullptr);
   for (int lev = t.jmin; lev < jx_star; ++lev) {
     int64_t nsp = 1;
@@ -1609,7 +1633,8 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
   ST_CUDA(h, cudaMemcpyAsync(t.comps, cc.data(), nc * sizeof(CombComp), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.tb, tb.data(), tb.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.tbw, tbw.data(), tbw.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-  ST_CUDA(h, cudaMemcpyAsync(t.dcomps, dc.data(), nc * sizeof(CombCompDS), cudaMemcpyHostToDevice, h->stream));
+  for (int b = 0; b < 2; ++b)
+    ST_CUDA(h, cudaMemcpyAsync(t.dcomps[b], dc[b].data(), nc * sizeof(CombCompDS), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaMemcpyAsync(t.span, tsp.data(), tsp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
   *out = &(h->comb[key] = t);
@@ -1617,8 +1642,11 @@ st_status comb_tables(st_handle* h, int jx_star, int jt_star, uint64_t mask, con
 }
 
 // One level of the hierarchical combination on the handle's stream.
+// buf: the pair buffer the level reads; prepped: the components' pairs were
+// already written into it on their own streams (st_solve_combine), otherwise
+// they are converted here on the handle's stream.
 void enqueue_comb_level(st_handle* h, const st_handle::CombTables& t, int lev, int jx_star, int jt_star,
-                        double* out_dev) {
+                        double* out_dev, int buf = 0, bool prepped = false) {
   const st_problem& p = h->prob;
   const int nts = (1 << jt_star) + 1;
   const int c0 = t.first[lev], c1 = t.first[lev + 1];
@@ -1632,13 +1660,15 @@ void enqueue_comb_level(st_handle* h, const st_handle::CombTables& t, int lev, i
   const double flops = (double)nsp * nts * ((Yp ? 1.0 : 0.0) + 6.0 * (c1 - c0));
   if (t.ds_ok) {
     // this level's components as pairs (sign applied, u0 folded in), then the level
-    for (int o = c0; o < c1; ++o) {
-      const Component& k = *h->comps[t.order[o]];
-      launch_comb_prep_ds(p.d, k.U, k.sl->lift, k.coef, k.jx, k.nt, k.Uds, k.Lds, h->stream);
-    }
+    if (!prepped)
+      for (int o = c0; o < c1; ++o) {
+        const Component& k = *h->comps[t.order[o]];
+        launch_comb_prep_ds(p.d, k.U, k.sl->lift, k.coef, k.jx, k.nt, k.Uds[buf], nullptr, h->stream);
+      }
     const int L = comb_ds_chunk(p.d, lev, jt_star, t.jt.data() + c0, c1 - c0);
     PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
-         launch_comb_level_ds(p.d, lev, Yp, t.dcomps, c0, c1, t.tbw, t.span, nts, L, Y, lev == jx_star, h->stream));
+         launch_comb_level_ds(p.d, lev, Yp, t.dcomps[buf], c0, c1, t.tbw, t.span, nts, L, Y, lev == jx_star,
+                              h->stream));
   } else {
     PROF(h, h->stream, KC_COMBINE, (int64_t)(nsp), outb + inb, flops,
          launch_comb_level(p.d, lev, Yp, t.comps, c0, c1, t.tb, t.span, nts, Y, h->stream));
@@ -1792,7 +1822,9 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
     g_create_error = "cudaMemset failed";
     return ST_ERR_CUDA;
   }
-  if (cudaEventCreateWithFlags(&hp->entry_ev, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&hp->entry_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&hp->sc_done_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&hp->sc_done_ev[1], cudaEventDisableTiming) != cudaSuccess) {
     g_create_error = "event creation failed";
     return ST_ERR_CUDA;
   }
@@ -1938,6 +1970,7 @@ st_status st_component(const st_handle* h, int k, st_component_info* info) {
 
 st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
   if (!h) return ST_ERR_ARG;
+  ++h->api_seq;
   if (k < -1 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
   const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? (int)h->comps.size() : k + 1;
   return run_solves(h, k0, k1, false, info);
@@ -1960,6 +1993,7 @@ st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_
   for (int i = 0; i < n; ++i) {
     st_handle* h = hs[i];
     ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+    ++h->api_seq;
     for (int k = 0; k < (int)h->comps.size(); ++k) {
       Component& c = *h->comps[k];
       c.err.clear();
@@ -2017,6 +2051,7 @@ st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
 
 st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* comps, int ncomp, double* out_dev) {
   if (!h || !out_dev || !comps || ncomp < 1) return ST_ERR_ARG;
+  ++h->api_seq;
   if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
   if (h->comps.size() > 64) return fail(h, ST_ERR_ARG, "more than 64 components");
   uint64_t mask = 0;
@@ -2036,21 +2071,40 @@ st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* c
 
 st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_dev, st_solve_info* info) {
   if (!h || !out_dev) return ST_ERR_ARG;
+  ++h->api_seq;
   if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
   if (h->comps.size() > 64) return fail(h, ST_ERR_ARG, "more than 64 components");
   const int nc = (int)h->comps.size();
   const uint64_t mask = nc == 64 ? ~0ull : ((1ull << nc) - 1);
   const st_handle::CombTables* t = nullptr;
+  // a call that directly follows another st_solve_combine on this handle (no
+  // other call in between that enqueues work on its stream) may start its
+  // solves while the previous call's combination levels still run
+  const bool chained = h->sc_seq >= 0 && h->api_seq == h->sc_seq + 1;
   st_status s = comb_tables(h, jx_star, jt_star, mask, &t);
   if (s != ST_OK) return s;
+  h->sc_seq = -1;  // set again once this call has enqueued everything
+  const bool overlap = t->ds_ok;
+  const int buf = h->sc_parity;
   // every component on its own stream and host thread; each records its
   // completion event and reports; the combination levels are enqueued on the
   // handle's stream level by level, each as soon as the components it adds
-  // have finished (a level also follows the previous one on that stream)
-  ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
-  for (auto& c : h->comps) {
-    c->err.clear();
-    ST_CUDA(h, cudaStreamWaitEvent(c->cs, h->entry_ev, 0));
+  // have finished (a level also follows the previous one on that stream).
+  // The levels read pair copies of the components (buffer `buf`), written on
+  // the component's stream right after its solve: so the next call's solves
+  // may overwrite the components while these levels run, and only the call
+  // after that, which reuses buffer `buf`, waits for them.
+  if (overlap && chained) {
+    for (auto& c : h->comps) {
+      c->err.clear();
+      if (h->sc_done_rec[buf]) ST_CUDA(h, cudaStreamWaitEvent(c->cs, h->sc_done_ev[buf], 0));
+    }
+  } else {
+    ST_CUDA(h, cudaEventRecord(h->entry_ev, h->stream));
+    for (auto& c : h->comps) {
+      c->err.clear();
+      ST_CUDA(h, cudaStreamWaitEvent(c->cs, h->entry_ev, 0));
+    }
   }
   StepTrace trace;
   std::vector<cudaEvent_t> comp_ev(nc, nullptr);
@@ -2067,6 +2121,10 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
   auto run = [&](int i) {
     Component& c = *h->comps[i];
     st_status r = solve_one(h, c, forward_io(c), false);
+    if (r == ST_OK && overlap) {
+      launch_comb_prep_ds(h->prob.d, c.U, c.sl->lift, c.coef, c.jx, c.nt, c.Uds[buf], nullptr, c.cs);
+      r = ccheck(c, "combination pairs");
+    }
     if (r == ST_OK && cudaEventRecord(c.done, c.cs) != cudaSuccess) r = cfail(c, ST_ERR_CUDA, "event record failed");
     if (comp_ev[i] != nullptr) cudaEventRecord(comp_ev[i], c.cs);
     {
@@ -2098,7 +2156,7 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     if (failed) break;
     cudaEvent_t lb = trace.t0 ? trace.make("level " + std::to_string(lev) + " combination start") : nullptr;
     if (lb != nullptr) cudaEventRecord(lb, h->stream);
-    enqueue_comb_level(h, *t, lev, jx_star, jt_star, out_dev);
+    enqueue_comb_level(h, *t, lev, jx_star, jt_star, out_dev, buf, overlap);
     cudaEvent_t le = trace.t0 ? trace.make("level " + std::to_string(lev) + " combination end") : nullptr;
     if (le != nullptr) cudaEventRecord(le, h->stream);
   }
@@ -2123,6 +2181,12 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
   }
   agg.status = worst;
   if (worst == ST_OK && failed) worst = fail(h, ST_ERR_CUDA, "stream wait failed");
+  if (worst == ST_OK && overlap) {
+    ST_CUDA(h, cudaEventRecord(h->sc_done_ev[buf], h->stream));
+    h->sc_done_rec[buf] = true;
+    h->sc_parity ^= 1;
+    h->sc_seq = h->api_seq;
+  }
   trace.report(h->stream);
   if (info) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
@@ -2134,6 +2198,7 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
 
 st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev) {
   if (!h || !x_rec || !out_dev || n_rec < 1) return ST_ERR_ARG;
+  ++h->api_seq;
   if (jt_star < 0 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target time level");
   for (auto& c : h->comps)
     if (!c->solved) return fail(h, ST_ERR_STATE, "receiver values before every component is solved");
@@ -2147,6 +2212,7 @@ st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int
 st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int n_rec, const double* d_obs_dev,
                              int jp, double* J_out, double* dc2_dev, double* dg_dev, st_solve_info* info) {
   if (!h || !x_rec || !d_obs_dev || n_rec < 1 || !J_out || !dc2_dev || !dg_dev) return ST_ERR_ARG;
+  ++h->api_seq;
   const st_problem& p = h->prob;
   if (jt_star < 0 || jt_star > 14 || jp < 0 || jp > 12) return fail(h, ST_ERR_ARG, "bad level");
   if (p.u0.fn != nullptr) return fail(h, ST_ERR_ARG, "the c^2 gradient is implemented for u0 = 0 only");
@@ -2215,6 +2281,7 @@ st_status st_tuned_shapes(int* out, int max_entries, int* n_out) {
 
 st_status st_component_coeffs(st_handle* h, int k, double* host_out) {
   if (!h || !host_out || k < 0 || k >= (int)h->comps.size()) return ST_ERR_ARG;
+  ++h->api_seq;
   Component& c = *h->comps[k];
   if (!c.solved) return fail(h, ST_ERR_STATE, "component not solved");
   ST_CUDA(h, cudaMemcpyAsync(host_out, c.U, (size_t)c.nx * c.nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -2249,6 +2316,7 @@ st_status st_kernel_launches(const st_handle* h, int64_t* count) {
 
 st_status st_profile(st_handle* h, int enable) {
   if (!h) return ST_ERR_ARG;
+  ++h->api_seq;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, ST_ERR_CUDA, "stream synchronisation failed");
   for (auto& r : h->prof) {
     h->ev_pool.push_back(r.a);

@@ -311,3 +311,28 @@ def test_solve_combine_overlapped_matches_separate_calls(prec):
     comps, sols = osolve.solve_all(p, method="schur")
     pts, times = osolve.target_grid(p, *target)
     assert _rel(a, osolve.combine(p, comps, sols, pts, times)) < (TOL64 if prec == 0 else TOL32)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_back_to_back_solve_combine_calls_overlap_correctly(prec):
+    """Consecutive st_solve_combine calls on one handle, with no synchronisation in
+    between, overlap the next call's solves with the previous call's combination
+    levels (the levels read pair copies of the components, double-buffered).  Three
+    queued calls with different targets and outputs give exactly the targets of
+    separate, synchronised calls."""
+    import torch
+    from paper_2606_09688_gb300 import Solver
+    p = W.layered_2d(9, 2)
+    targets = [(7, 7), (6, 5), (7, 7), (5, 6)]
+    with Solver(p, precision=prec) as s:
+        ref = []
+        for t in targets:
+            out, info = s.solve_combine(*t)
+            assert info.status == 0
+            ref.append(out.cpu().numpy())
+            s.solve(0)                 # another call in between: the next one starts afresh
+        outs = [s.solve_combine(*t, sync=False)[0] for t in targets]
+        torch.cuda.synchronize()
+        got = [o.cpu().numpy() for o in outs]
+    for a, b in zip(got, ref):
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
