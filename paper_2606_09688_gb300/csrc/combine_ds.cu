@@ -30,6 +30,7 @@ namespace {
 constexpr int kCombThreads = 256;
 constexpr int kCombMaxChunk = 256;
 constexpr int kCombRegComps = 2;  // components held in registers per level
+constexpr int kCombChunk = 32;     // target times per CTA (at most kCombMaxChunk)
 
 // comps[c]: the component's coefficient pairs, the sign of its coefficient
 // applied and u0 folded in (U_ds[i][a] = coef (U[i][a] + u0(x_a))), and
@@ -256,8 +257,11 @@ void launch_ds_d(int nr, bool final_level, dim3 grid, int j, const ds* Yprev, co
 
 int comb_ds_chunk(int d, int j, int jt_star, const int* comp_jt, int ncomp_level) {
   const int nts1 = 1 << jt_star;  // target time intervals
-  // chunks aligned to every register-held component's time intervals
-  int L = kCombMaxChunk < nts1 ? kCombMaxChunk : nts1;
+  // chunks aligned to every register-held component's time intervals, and
+  // short enough that a CTA finishes within tens of microseconds (so that
+  // the solves of the next step, queued at a higher stream priority, find
+  // free SM slots quickly while a level runs)
+  int L = kCombChunk < nts1 ? kCombChunk : nts1;
   for (int r = 0; r < ncomp_level && r < kCombRegComps; ++r) {
     const int gap = jt_star - comp_jt[r];
     const int span_len = gap <= 0 ? 1 : (gap >= 30 ? (1 << 30) : (1 << gap));
