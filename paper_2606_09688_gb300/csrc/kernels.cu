@@ -243,6 +243,198 @@ __global__ void __launch_bounds__(256) k_stencil_tile2(Geo g, StencilCoefT<R> sc
   }
 }
 
+// 2D variant streaming down columns: a warp owns 30 consecutive columns of
+// interior nodes (its lanes 0 and 31 hold the halo columns) and walks a strip
+// of `rows` rows (32 on large grids, fewer on small ones, so that small grids
+// still spread over many warps).  The x values of rows i-1, i, i+1 and the c^2 cells of
+// cell rows i, i+1 roll in registers; the left and right neighbours of a new
+// row come from the adjacent lanes through a small shared-memory row per warp
+// (double-buffered).  Per node and mode the kernel reads x and b once and
+// writes y once (three global requests instead of nine).  The loads of x, b
+// and c^2 run PF rows ahead of the row being computed, so that a warp keeps
+// PF rows of requests in flight instead of waiting one load latency per row.
+constexpr int kColWarps = 4, kColOut = 30;
+template <typename R, int OP, int MQ>
+__global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
+                                                                  const cx<R>* __restrict__ x,
+                                                                  const cx<R>* __restrict__ b, cx<R>* __restrict__ y,
+                                                                  const cx<R>* __restrict__ lam,
+                                                                  const CocgScal* __restrict__ scal, int nmodes,
+                                                                  int64_t stride, R omega, int rows) {
+  constexpr int PF = MQ >= 4 ? 1 : (MQ == 2 ? 2 : 4);  // rows of loads in flight ahead of the computed row
+  __shared__ cx<R> srow[kColWarps][2][MQ][32];
+  __shared__ R scell[kColWarps][2][32];
+  const int n = g.n, N = g.N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ix = (blockIdx.x * kColWarps + warp) * kColOut - 1 + lane;
+  const int r0 = blockIdx.y * rows;
+  const int q0 = blockIdx.z * MQ;
+  const bool colok = ix >= 0 && ix < n;
+  const bool cellok = ix >= 0 && ix < N;
+  const bool writer = lane >= 1 && lane <= kColOut && colok;
+  const int lm1 = lane > 0 ? lane - 1 : 0, lp1 = lane < 31 ? lane + 1 : 31;
+  const cx<R> zero = mk<R>(0, 0);
+  bool act[MQ];
+  const cx<R>* xq[MQ];
+  const cx<R>* bq[MQ];
+#pragma unroll
+  for (int m = 0; m < MQ; ++m) {
+    const int q = q0 + m;
+    act[m] = q < nmodes && (scal == nullptr || scal[q].active);
+    xq[m] = x + (int64_t)(act[m] ? q : 0) * stride;
+    bq[m] = b + (int64_t)(act[m] ? q : 0) * stride;
+  }
+  auto ldx = [&](int m, int row) -> cx<R> {
+    return (act[m] && colok && row >= 0 && row < n) ? xq[m][(int64_t)row * n + ix] : zero;
+  };
+  auto ldb = [&](int m, int row) -> cx<R> {
+    return (OP != OP_APPLY && act[m] && writer && row < n) ? bq[m][(int64_t)row * n + ix] : zero;
+  };
+  auto ldc = [&](int row) -> R { return (cellok && row >= 0 && row < N) ? c2[(int64_t)row * N + ix] : R(0); };
+  // rows r0-1, r0, r0+1 of x, cell rows r0, r0+1, and the queues of the next PF rows
+  cx<R> xa[MQ], xb[MQ], xc[MQ], xf[PF][MQ], bf[PF][MQ];
+  R cf[PF];
+#pragma unroll
+  for (int m = 0; m < MQ; ++m) {
+    xa[m] = ldx(m, r0 - 1);
+    xb[m] = ldx(m, r0);
+    xc[m] = ldx(m, r0 + 1);
+  }
+  R ca = ldc(r0), cb = ldc(r0 + 1);
+#pragma unroll
+  for (int f = 0; f < PF; ++f) {
+#pragma unroll
+    for (int m = 0; m < MQ; ++m) {
+      xf[f][m] = ldx(m, r0 + 2 + f);
+      bf[f][m] = ldb(m, r0 + f);
+    }
+    cf[f] = ldc(r0 + 2 + f);
+  }
+  // neighbours (left, right) of rows r0-1 and r0 through the row buffers
+  cx<R> la[MQ], ra[MQ], lb[MQ], rb[MQ], lc[MQ], rc[MQ];
+  R car, cbr;  // cells of column ix + 1
+  {
+#pragma unroll
+    for (int m = 0; m < MQ; ++m) {
+      srow[warp][0][m][lane] = xa[m];
+      srow[warp][1][m][lane] = xb[m];
+    }
+    scell[warp][0][lane] = ca;
+    scell[warp][1][lane] = cb;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MQ; ++m) {
+      la[m] = srow[warp][0][m][lm1];
+      ra[m] = srow[warp][0][m][lp1];
+      lb[m] = srow[warp][1][m][lm1];
+      rb[m] = srow[warp][1][m][lp1];
+    }
+    car = scell[warp][0][lp1];
+    cbr = scell[warp][1][lp1];
+    __syncwarp();
+  }
+  int buf = 0;
+  const int rend = min(r0 + rows, n);
+  // rows in groups of PF: queue slot f is refilled right after it is used,
+  // with no register moves of loads still in flight
+  for (int row0 = r0; row0 < rend; row0 += PF) {
+#pragma unroll
+    for (int f = 0; f < PF; ++f) {
+      const int row = row0 + f;
+      if (row >= rend) break;
+      // neighbours of row + 1 and of its cells' next row (slot f: rows row + 2)
+#pragma unroll
+      for (int m = 0; m < MQ; ++m) srow[warp][buf][m][lane] = xc[m];
+      scell[warp][buf][lane] = cf[f];
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < MQ; ++m) {
+        lc[m] = srow[warp][buf][m][lm1];
+        rc[m] = srow[warp][buf][m][lp1];
+      }
+      const R cnr = scell[warp][buf][lp1];
+      if (writer) {
+        // cells of the node (ix, row): (ix, row), (ix+1, row), (ix, row+1), (ix+1, row+1)
+        const R c00 = ca, c10 = car, c01 = cb, c11 = cbr;
+        R kr[9];
+        kr[0] = c00;
+        kr[1] = c00 + c10;
+        kr[2] = c10;
+        kr[3] = c00 + c01;
+        kr[4] = (c00 + c10) + (c01 + c11);
+        kr[5] = c10 + c11;
+        kr[6] = c01;
+        kr[7] = c01 + c11;
+        kr[8] = c11;
+#pragma unroll
+        for (int s2 = 0; s2 < 9; ++s2) kr[s2] *= sc.ke[s2];
+        const int64_t a = (int64_t)row * n + ix;
+#pragma unroll
+        for (int m = 0; m < MQ; ++m) {
+          if (!act[m]) continue;
+          const int q = q0 + m;
+          const cx<R> l = lam[q];
+          const int64_t base = (int64_t)q * stride + a;
+          const cx<R> v[9] = {la[m], xa[m], ra[m], lb[m], xb[m], rb[m], lc[m], xc[m], rc[m]};
+          cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
+#pragma unroll
+          for (int s2 = 0; s2 < 9; ++s2) {
+            ak = fma_s(kr[s2], v[s2], ak);
+            am = fma_s(sc.mtot[s2], v[s2], am);
+          }
+          const cx<R> Ax = fma_c(l, am, ak);
+          if (OP == OP_APPLY) {
+            y[base] = Ax;
+          } else if (OP == OP_RESID) {
+            y[base] = bf[f][m] - Ax;
+          } else {  // OP_JACOBI
+            const cx<R> diag = fma_s(sc.mtot[4], l, mk<R>(kr[4], R(0)));
+            y[base] = xb[m] + scaled_div(omega, bf[f][m] - Ax, diag);
+          }
+        }
+      }
+      // roll the rows; refill slot f PF rows ahead
+#pragma unroll
+      for (int m = 0; m < MQ; ++m) {
+        xa[m] = xb[m];
+        la[m] = lb[m];
+        ra[m] = rb[m];
+        xb[m] = xc[m];
+        lb[m] = lc[m];
+        rb[m] = rc[m];
+        xc[m] = xf[f][m];
+        xf[f][m] = ldx(m, row + 2 + PF);
+        bf[f][m] = ldb(m, row + PF);
+      }
+      ca = cb;
+      car = cbr;
+      cb = cf[f];
+      cbr = cnr;
+      cf[f] = ldc(row + 2 + PF);
+      buf ^= 1;
+    }
+  }
+}
+
+template <typename R, int MQ>
+void stencil_col2_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
+                     cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
+                     cudaStream_t s) {
+  const int warps = (g.n + kColOut - 1) / kColOut;
+  const int rows = g.n >= 512 ? 32 : (g.n >= 128 ? 16 : 8);
+  const dim3 grid((warps + kColWarps - 1) / kColWarps, (g.n + rows - 1) / rows, (nmodes + MQ - 1) / MQ);
+  const R om = (R)omega;
+  if (op == OP_APPLY)
+    k_stencil_col2<R, OP_APPLY, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om,
+                                                                    rows);
+  else if (op == OP_RESID)
+    k_stencil_col2<R, OP_RESID, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om,
+                                                                    rows);
+  else
+    k_stencil_col2<R, OP_JACOBI, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride,
+                                                                     om, rows);
+}
+
 template <typename R, int MQ>
 void stencil_tile2_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                       cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
@@ -306,7 +498,9 @@ template <int D> StencilShape default_shape(int64_t nnodes, int nmodes) {
   return StencilShape{mq, kBlock};
 }
 
-// block == 0 selects the shared-memory tile kernel (2D, operations that read x).
+// block == 0 selects the shared-memory tile kernel, block == kColBlockCode the
+// column-streaming kernel (both 2D, operations that read x).
+constexpr int kColBlockCode = 64;
 template <int D, typename R>
 void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x,
                           const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
@@ -315,6 +509,12 @@ void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const
     if (sh.mq == 4) stencil_tile2_mq<R, 4>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else if (sh.mq == 2) stencil_tile2_mq<R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else stencil_tile2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    return;
+  }
+  if (sh.block == kColBlockCode && D == 2 && op != OP_JACOBI_ZERO) {
+    if (sh.mq == 4) stencil_col2_mq<R, 4>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    else if (sh.mq == 2) stencil_col2_mq<R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    else stencil_col2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     return;
   }
   if (sh.mq == 4 && D < 3)
@@ -345,7 +545,7 @@ template <int D, typename R>
 float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                    cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s) {
   const int mqs[3] = {1, 2, 4};
-  const int blocks[4] = {128, 256, 512, 0};  // 0: the shared-memory tile kernel (2D)
+  const int blocks[5] = {128, 256, 512, 0, kColBlockCode};  // 0: shared-memory tiles, 64: column streaming (2D)
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -358,7 +558,7 @@ float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
     if (D == 3 && mq > 2) continue;
     if (mq > 1 && mq > 2 * nmodes) continue;
     for (int bk : blocks) {
-      if (bk == 0 && (D != 2 || op == OP_JACOBI_ZERO)) continue;
+      if ((bk == 0 || bk == kColBlockCode) && (D != 2 || op == OP_JACOBI_ZERO)) continue;
       const StencilShape sh{mq, bk};
       float t[3];
       stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, nullptr, nmodes, stride, omega, sh, s);
@@ -1580,8 +1780,8 @@ bool set_stencil_shape(int op, int d, int rsize, int64_t nnodes, int nmodes, int
   if (op < 0 || op > 3 || d < 1 || d > 3 || (rsize != 4 && rsize != 8) || nnodes < 1 || nmodes < 1) return false;
   if (mq != 1 && mq != 2 && mq != 4) return false;
   if (d == 3 && mq == 4) return false;
-  if (block != 0 && block != 128 && block != 256 && block != 512) return false;
-  if (block == 0 && (d != 2 || op == OP_JACOBI_ZERO)) return false;
+  if (block != 0 && block != kColBlockCode && block != 128 && block != 256 && block != 512) return false;
+  if ((block == 0 || block == kColBlockCode) && (d != 2 || op == OP_JACOBI_ZERO)) return false;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune[std::make_tuple(op, d, rsize, nnodes, nmodes)] = StencilShape{mq, block};
   return true;

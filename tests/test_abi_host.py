@@ -197,7 +197,10 @@ def test_tuned_shape_pinning_validates_the_shape():
     good = dict(op=2, d=2, elem_bytes=4, nodes=12345, modes=3, modes_per_thread=2, block=0)
     set_tuned_shape(good)
     assert good in tuned_shapes()
-    for bad in (dict(good, modes_per_thread=3), dict(good, block=64), dict(good, d=3, block=0),
+    set_tuned_shape(dict(good, block=64))
+    assert dict(good, block=64) in tuned_shapes()
+    for bad in (dict(good, modes_per_thread=3), dict(good, block=96), dict(good, d=3, block=0),
+                dict(good, d=3, block=64), dict(good, op=3, block=64),
                 dict(good, op=3, block=0), dict(good, d=3, modes_per_thread=4, block=256),
                 dict(good, elem_bytes=2), dict(good, nodes=0)):
         with pytest.raises(StError):

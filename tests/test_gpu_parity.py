@@ -259,7 +259,8 @@ def test_solve_batch_matches_separate_solves():
 def test_autotuned_launch_shapes_keep_the_results():
     """Multigrid on a 127^2 grid (direct limit lowered so that it is not solved
     directly): with the built-in shapes, the autotuned shapes, and every 2D key
-    pinned to the shared-memory tile kernel, the combination matches the oracle."""
+    pinned to the shared-memory tile kernel and then to the column-streaming
+    kernel, the combination matches the oracle."""
     from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64, Solver, StError
     from paper_2606_09688_gb300.st import set_tuned_shape, tuned_shapes
     p = W.layered_2d(9, 2)
@@ -279,15 +280,16 @@ def test_autotuned_launch_shapes_keep_the_results():
     shapes = tuned_shapes()
     assert any(e["nodes"] == 127 * 127 for e in shapes)
     for e in shapes:
-        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (0, 128, 256, 512)
-    pinned = 0
-    for e in shapes:
-        if e["d"] == 2 and e["op"] != 3:
-            set_tuned_shape(dict(e, block=0))
-            pinned += 1
-    assert pinned > 0
-    for prec in (ST_FP64, ST_FP32_IR):
-        assert _rel(run(prec, -1), ref) < (TOL64 if prec == ST_FP64 else TOL32)
+        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (0, 64, 128, 256, 512)
+    for kernel in (0, 64):        # the shared-memory tile kernel, then the column-streaming kernel
+        pinned = 0
+        for e in shapes:
+            if e["d"] == 2 and e["op"] != 3:
+                set_tuned_shape(dict(e, block=kernel))
+                pinned += 1
+        assert pinned > 0
+        for prec in (ST_FP64, ST_FP32_IR):
+            assert _rel(run(prec, -1), ref) < (TOL64 if prec == ST_FP64 else TOL32), kernel
     with pytest.raises(StError):
         set_tuned_shape(dict(shapes[0], modes_per_thread=3))
 
