@@ -118,3 +118,54 @@ def test_sharded_combination_gloo_matches_the_full_sum(world):
         owned += ks
         assert np.max(np.abs(got - full)) <= 1e-13 * np.max(np.abs(full))
     assert sorted(owned) == list(range(len(comps)))   # every component solved by exactly one rank
+
+
+class FailingSolver(OracleSolver):
+    """A solver whose first solve raises (a failed component on one rank)."""
+
+    def solve(self, k, sync=True):
+        raise RuntimeError("component solve failed on this rank")
+
+
+def _rank_main_failing(rank, world, port, results):
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    p = W.e2_variable_speed(3)
+    solver = FailingSolver(p) if rank == 1 else OracleSolver(p)
+    out = torch.zeros(((1 << 3) + 1, (1 << 3) + 1), dtype=torch.float64)
+    try:
+        shard.sharded_combine(solver, 3, 3, out, rank, world)
+        results[rank] = "completed"
+    except Exception as e:  # the failing rank's own error, or the collective's on the others
+        results[rank] = "error: " + type(e).__name__
+        if rank == 1:
+            raise          # the failed rank leaves (process exit code != 0)
+    finally:
+        if rank == 0:
+            try:
+                dist.destroy_process_group()
+            except Exception:
+                pass
+
+
+def test_a_failed_rank_is_detected_by_the_others():
+    """Rank 1 fails before the sum-reduction of the sharded combination; rank 0 does not
+    hang in the collective: the collective ends with an error (peer gone or timeout)."""
+    import time
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    results = mgr.dict()
+    t0 = time.time()
+    ctx = mp.start_processes(_rank_main_failing, args=(world, _free_port(), results), nprocs=world,
+                             start_method="spawn", join=False)
+    for p in ctx.processes:
+        p.join(timeout=120)
+    codes = [p.exitcode for p in ctx.processes]
+    for p in ctx.processes:
+        if p.is_alive():
+            p.kill()
+    assert codes[1] not in (0, None)                      # the failed rank exited with an error
+    assert codes[0] == 0 and results[0].startswith("error")  # the other rank saw the failure and returned
+    assert time.time() - t0 < 120
