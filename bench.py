@@ -73,6 +73,8 @@ def parse():
                     help="profiling aid: each step solves only this component (no combination)")
     ap.add_argument("--target", default="",
                     help="profiling aid: target levels 'jx,jt' in place of the workload's")
+    ap.add_argument("--device-loop", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="inner Krylov loop on the device (iterations per graph body; 0 = host-checked)")
     return ap.parse_args()
 
 
@@ -430,7 +432,7 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
             solver = Solver(problem, precision=code, stream=stream, inner_tol=args.inner_tol,
-                            max_direct_rows=args.max_direct_rows)
+                            max_direct_rows=args.max_direct_rows, device_loop=args.device_loop)
             setup_s = time.perf_counter() - t0
             solver._bench_out = out
             r = measure(solver, target, args.steps, args.warmup, stream, torch, barrier, maxall,
@@ -506,7 +508,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": sig(head["ms"]), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "target": list(target), "dofs": head["dofs"],
-                   "l2": "target grid written each step > L2"},
+                   "l2": "target grid written each step > L2", "device_loop": args.device_loop},
         "gpu_launches": head["launches"],
         "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons")},
         "roofline": compact_roofline(rl),

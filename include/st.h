@@ -119,6 +119,13 @@ typedef struct {
                            never issued, so its bounded wait runs out after
                            wait_cycles and the solve returns ST_ERR_TIMEOUT;
                            0 = off (default) */
+  int device_loop;      /* inner Krylov loop of the multigrid components:
+                           0 = graph launches of 4 iterations with a host check
+                           of convergence after each (default); k = 4, 8 or 16 =
+                           the whole loop on the device as one CUDA graph with a
+                           conditional WHILE node whose body runs k iterations
+                           and tests convergence on the device (no host round
+                           trip until the refinement sweep's norms) */
 } st_options;
 
 typedef struct {

@@ -1673,6 +1673,23 @@ void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, in
   k_gemm_right<<<grid, block, 0, s>>>(X, Phi, Y, nt, nx, accumulate);
 }
 
+// Condition of the device-side COCG loop (a WHILE node of a CUDA graph):
+// continue while any mode is still iterating.  Every mode leaves the active
+// set at convergence, at a breakdown or at its iteration limit, so the loop
+// ends after at most max_iter / (iterations per body) + 1 bodies.  One thread
+// sets the condition (concurrent calls would race).
+__global__ void k_cocg_continue(const CocgScal* __restrict__ scal, int nmodes, cudaGraphConditionalHandle handle) {
+  int any = 0;
+  for (int q = threadIdx.x; q < nmodes; q += blockDim.x) any |= scal[q].active;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, cudaStream_t s) {
+  count(1);
+  k_cocg_continue<<<1, 128, 0, s>>>(scal, nmodes, handle);
+}
+
 size_t time_band_smem(int nt) { return (size_t)nt * (7 * sizeof(double) + sizeof(double) + sizeof(int)); }
 
 bool launch_time_band_solve(const double* ab, const int* piv, double* Y, int nt, int64_t nx, int kl, int ku,

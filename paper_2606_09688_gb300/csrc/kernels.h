@@ -48,6 +48,8 @@ template <typename R>
 void launch_update_p(cx<R>* p, const cx<R>* z, const CocgScal* scal, int nmodes, int64_t n, int64_t stride,
                      int first, cudaStream_t s);
 void launch_cocg_activate(CocgScal* scal, int nmodes, cudaStream_t s);
+// Sets the condition of a graph WHILE node: non-zero while any mode is active.
+void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, cudaStream_t s);
 
 // Time transforms of the eigenbasis method (FP64 matrices):
 // G[q][a] = sum_i W[q][i] R[i][a];  U[i][a] += sum_q w_q Re(V[i][q] X[q][a]).

@@ -248,6 +248,13 @@ struct Component {
   // iterations, captured at setup on the component stream.
   cudaGraphExec_t g_init = nullptr, g_iter = nullptr;
   int64_t g_init_nodes = 0, g_iter_nodes = 0;
+  // the whole inner loop on the device: a WHILE node whose body is
+  // kIterPerGraph iterations and the test "any mode still active"
+  cudaGraphExec_t g_while = nullptr;
+  int64_t g_while_nodes = 0;       // kernels per body execution
+  int g_while_body = 0;            // COCG iterations per body
+  bool inner_pending = false;      // a device-side loop ran; its status is read after the next sync
+  double fnorm = -1.0;             // ||F|| of the forward right-hand side (constant after setup)
 };
 
 // Algorithmic flops per node of the complex Q1 stencil (K and M parts with
@@ -341,6 +348,7 @@ struct st_handle {
     for (auto& c : comps) {
       if (c->g_init) cudaGraphExecDestroy(c->g_init);
       if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
+      if (c->g_while) cudaGraphExecDestroy(c->g_while);
       if (c->cscalar_h) cudaFreeHost(c->cscalar_h);
       if (c->cs) cudaStreamDestroy(c->cs);
       if (c->done) cudaEventDestroy(c->done);
@@ -1216,7 +1224,65 @@ template <typename R> st_status capture_graphs(st_handle* h, Component& c) {
       c.g_iter_nodes = nodes;
     }
   }
+  // the device-side loop: WHILE (any mode active) { k iterations; update the condition }
+  if (h->opt.device_loop > 0) {
+    cudaGraph_t wg = nullptr;
+    ST_CUDA(h, cudaGraphCreate(&wg, 0));
+    cudaGraphConditionalHandle hnd;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hnd, wg, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.conditional.handle = hnd;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&node, wg, nullptr, nullptr, 0, &cp);
+    }
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(wg);
+      return fail(h, ST_ERR_CUDA, std::string("conditional graph node: ") + cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const int64_t l0 = kernel_launch_count();
+    ST_CUDA(h, cudaStreamBeginCaptureToGraph(c.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < h->opt.device_loop; ++k) cocg_iteration<R>(h, c);
+    launch_cocg_continue(c.scal, c.nsel, hnd, c.cs);
+    cudaGraph_t captured = nullptr;
+    ST_CUDA(h, cudaStreamEndCapture(c.cs, &captured));
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, wg, 0);
+    cudaGraphDestroy(wg);
+    if (e != cudaSuccess) return fail(h, ST_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+    c.g_while = ge;
+    c.g_while_nodes = kernel_launch_count() - l0;
+    c.g_while_body = h->opt.device_loop;
+  }
   return check_launch(h, "graph capture");
+}
+
+// Status of a device-side inner loop (st_solve_component's COCG run as one
+// graph launch): read after the stream has been synchronised by the caller.
+st_status check_inner(Component& c, int& iters_out) {
+  iters_out = 0;
+  if (!c.inner_pending) return ST_OK;
+  c.inner_pending = false;
+  ST_CUDAC(c, cudaMemcpy(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost));
+  c.d2h += (int64_t)(c.nsel * sizeof(CocgScal));
+  int worst = 0;
+  for (const auto& q : c.scal_h) {
+    iters_out = std::max(iters_out, q.iters);
+    if (q.status != 0) worst = q.status;
+  }
+  // the loop body ran once per `device_loop` iterations of the slowest mode
+  // (one body was counted at launch)
+  if (c.g_while_body > 0) {
+    const int bodies = std::max(1, (iters_out + c.g_while_body - 1) / c.g_while_body);
+    note_launches((int)(c.g_while_nodes * (bodies - 1)));
+  }
+  if (worst == 4) return cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
+  if (worst != 0) return cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
+  return ST_OK;
 }
 
 // Solve (lam_q M + K) x_q = g_q for every mode; w.G holds g, the result lands in w.X.
@@ -1234,6 +1300,15 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
     return ccheck(c, "direct band solve");
   }
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
+  if (!h->prof_on && c.g_init != nullptr && c.g_while != nullptr) {
+    // the whole loop on the device: no host round trip; the modes' status
+    // words are read after the sweep's norms (check_inner)
+    ST_CUDAC(c, cudaGraphLaunch(c.g_init, s));
+    ST_CUDAC(c, cudaGraphLaunch(c.g_while, s));
+    note_launches((int)(c.g_init_nodes + c.g_while_nodes));
+    c.inner_pending = true;
+    return ST_OK;
+  }
   const bool graphs = !h->prof_on && c.g_init != nullptr && c.g_iter != nullptr;
   if (graphs) {
     ST_CUDAC(c, cudaGraphLaunch(c.g_init, s));
@@ -1263,6 +1338,12 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
     iters_out = std::max(iters_out, q.iters);
     if (q.status != 0) worst = q.status;
   }
+  // the loop body ran once per `device_loop` iterations of the slowest mode
+  // (one body was counted at launch)
+  if (c.g_while_body > 0) {
+    const int bodies = std::max(1, (iters_out + c.g_while_body - 1) / c.g_while_body);
+    note_launches((int)(c.g_while_nodes * (bodies - 1)));
+  }
   if (worst == 4) return cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
   if (worst != 0) return cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
   return ST_OK;
@@ -1278,6 +1359,21 @@ st_status assemble_rhs(st_handle* h, Component& c) {
                   1.0, 1, c.cs);
   c.f_ready = true;
   return ccheck(c, "rhs");
+}
+
+// ||a|| and ||b|| (2-norms) with one synchronisation.
+st_status read_norm2(st_handle* h, Component& c, const double* a, const double* b, int64_t n, double& na, double& nb) {
+  PROF(h, c.cs, KC_NORM, (int64_t)(n), (double)n * 8.0, 2.0 * n, launch_norm2(a, n, c.cpart, c.cscalar, c.cs));
+  PROF(h, c.cs, KC_NORM, (int64_t)(n), (double)n * 8.0, 2.0 * n, launch_norm2(b, n, c.cpart, c.cscalar + 1, c.cs));
+  int serr = 0;
+  ST_CUDAC(c, cudaMemcpyAsync(&serr, c.cerr, sizeof(int), cudaMemcpyDeviceToHost, c.cs));
+  ST_CUDAC(c, cudaMemcpyAsync(c.cscalar_h, c.cscalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.cs));
+  c.d2h += (int64_t)(2 * sizeof(double) + sizeof(int));
+  ST_CUDAC(c, cudaStreamSynchronize(c.cs));
+  na = std::sqrt(c.cscalar_h[0]);
+  nb = std::sqrt(c.cscalar_h[1]);
+  if (serr) return cfail(c, ST_ERR_TIMEOUT, "a bounded copy wait in the banded solve timed out");
+  return ccheck(c, "norm");
 }
 
 st_status read_norm(st_handle* h, Component& c, const double* v, int64_t n, double& out) {
@@ -1344,7 +1440,12 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
   const size_t n = (size_t)c.nx * c.nt;
   ST_CUDAC(c, cudaMemsetAsync(io.sol, 0, n * sizeof(double), c.cs));
   double fn = 0.0;
-  if ((s = read_norm(h, c, io.rhs, (int64_t)n, fn)) != ST_OK) return s;
+  if (!adjoint && c.fnorm >= 0.0) {
+    fn = c.fnorm;  // F is fixed after setup
+  } else {
+    if ((s = read_norm(h, c, io.rhs, (int64_t)n, fn)) != ST_OK) return s;
+    if (!adjoint) c.fnorm = fn;
+  }
   // Refinement stops on the normwise backward error eta = ||R|| / (||S|| ||U|| + ||F||)
   // (the relative residual of an exact solution can be far above rounding
   // when S is ill-conditioned), or when a sweep no longer halves eta.
@@ -1373,14 +1474,19 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
       return s;
     }
     c.info.sweeps = sw + 1;
-    c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
     PROF(h, c.cs, KC_RESIDUAL64, (int64_t)(c.nx), 7.0 * (double)n * 8.0 + (double)c.sl->geo.ncells * 8.0,
          (double)n * (4.0 * ipow3(c.sl->geo.d) + 20.0),
          launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, io.sol, io.rhs, io.Ab, io.Bb, c.KU, c.MU, c.Rv, c.nt,
                          c.cs));
     double rn = 0.0, un = 0.0;
-    if ((s = read_norm(h, c, c.Rv, (int64_t)n, rn)) != ST_OK) return s;
-    if ((s = read_norm(h, c, io.sol, (int64_t)n, un)) != ST_OK) return s;
+    if ((s = read_norm2(h, c, c.Rv, io.sol, (int64_t)n, rn, un)) != ST_OK) return s;
+    // the inner loop of this sweep ran on the device: its status words now
+    int dev_iters = 0;
+    if ((s = check_inner(c, dev_iters)) != ST_OK) {
+      c.info.status = s;
+      return s;
+    }
+    c.info.max_inner_iters = std::max(c.info.max_inner_iters, std::max(iters, dev_iters));
     rel = rn / fn;
     eta = rn / (c.Snorm * un + fn);
     if (!std::isfinite(rel)) {
@@ -1412,13 +1518,13 @@ st_status setup_context(st_handle* h, Component& c) {
   ST_CUDA(h, cudaStreamCreateWithPriority(&c.cs, cudaStreamNonBlocking, prio_hi));
   ST_CUDA(h, cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
   c.cpart = h->alloc<double>(304);
-  c.cscalar = h->alloc<double>(1);
+  c.cscalar = h->alloc<double>(2);
   c.cerr = h->alloc<int>(1);
   ST_NEED(h, c.cpart);
   ST_NEED(h, c.cscalar);
   ST_NEED(h, c.cerr);
   ST_CUDA(h, cudaMemsetAsync(c.cerr, 0, sizeof(int), h->stream));
-  ST_CUDA(h, cudaMallocHost(&c.cscalar_h, sizeof(double)));
+  ST_CUDA(h, cudaMallocHost(&c.cscalar_h, 2 * sizeof(double)));
   if (c.method == 0) {
     st_status s = c.inner64 ? prepare_work<double>(h, c) : prepare_work<float>(h, c);
     if (s != ST_OK) return s;
@@ -1805,6 +1911,8 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   if (h->opt.autotune < -1 || h->opt.autotune > 1) return fail(nullptr, ST_ERR_ARG, "autotune must be -1, 0 or 1");
   if (h->opt.mem_cap_bytes < 0 || h->opt.wait_cycles < 0 || h->opt.inject_stall < 0 || h->opt.inject_stall > 1)
     return fail(nullptr, ST_ERR_ARG, "mem_cap_bytes and wait_cycles must be >= 0, inject_stall 0 or 1");
+  if (h->opt.device_loop != 0 && h->opt.device_loop != 4 && h->opt.device_loop != 8 && h->opt.device_loop != 16)
+    return fail(nullptr, ST_ERR_ARG, "device_loop must be 0, 4, 8 or 16");
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->nterm_rows = p.n_terms + 2;
   h->launches0 = kernel_launch_count();

@@ -45,7 +45,7 @@ class StOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("max_sweeps", C.c_int),
                 ("stream", C.c_void_p), ("inner_tol", C.c_double), ("max_direct_rows", C.c_int),
                 ("autotune", C.c_int), ("mem_cap_bytes", C.c_int64), ("wait_cycles", C.c_int64),
-                ("inject_stall", C.c_int)]
+                ("inject_stall", C.c_int), ("device_loop", C.c_int)]
 
 
 class StComponentInfo(C.Structure):
@@ -154,7 +154,8 @@ class Solver:
 
     def __init__(self, problem, precision: int = ST_FP64, tol: float = 0.0, max_iter: int = 0,
                  max_sweeps: int = 0, stream=None, inner_tol: float = 0.0, max_direct_rows: int = 0,
-                 autotune: int = 0, mem_cap_bytes: int = 0, wait_cycles: int = 0, inject_stall: int = 0):
+                 autotune: int = 0, mem_cap_bytes: int = 0, wait_cycles: int = 0, inject_stall: int = 0,
+                 device_loop: int = 0):
         import torch
         self._lib = lib()
         p = problem
@@ -193,7 +194,7 @@ class Solver:
             stream = torch.cuda.current_stream()
         self.stream = stream
         opt = StOptions(precision, tol, max_iter, max_sweeps, C.c_void_p(stream.cuda_stream), inner_tol,
-                        max_direct_rows, autotune, mem_cap_bytes, wait_cycles, inject_stall)
+                        max_direct_rows, autotune, mem_cap_bytes, wait_cycles, inject_stall, device_loop)
         h = C.c_void_p()
         code = self._lib.st_setup(C.byref(prob), C.byref(opt), C.byref(h))
         if code != ST_OK:

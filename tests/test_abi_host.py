@@ -189,6 +189,10 @@ def test_setup_rejects_bad_solver_options_without_touching_the_gpu():
         assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
         assert b"inject_stall" in L.st_last_error(None)
         assert h.value is None
+    for loop in (-1, 3, 32):
+        opt = B.StOptions(B.ST_FP64, 0.0, 0, 0, None, 0.0, 0, 0, 0, 0, 0, loop)
+        assert L.st_setup(C.byref(prob), C.byref(opt), C.byref(h)) == B.ST_ERR_ARG
+        assert b"device_loop" in L.st_last_error(None)
 
 
 def test_tuned_shape_pinning_validates_the_shape():

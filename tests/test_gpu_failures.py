@@ -34,11 +34,13 @@ def _component(s, jx, jt):
     return next(k for k, ci in enumerate(s.components()) if (ci.jx, ci.jt) == (jx, jt))
 
 
-def test_inner_iteration_limit_reports_not_converged():
+@pytest.mark.parametrize("device_loop", [0, 4])
+def test_inner_iteration_limit_reports_not_converged(device_loop):
     from paper_2606_09688_gb300 import Solver, StError
     from paper_2606_09688_gb300 import st as B
-    # grids above 500 unknowns go through multigrid-preconditioned COCG
-    with Solver(W.layered_2d(8, 2), max_direct_rows=500, max_iter=1) as s:
+    # grids above 500 unknowns go through multigrid-preconditioned COCG; with the
+    # device-side loop the modes' status words are read after the sweep
+    with Solver(W.layered_2d(8, 2), max_direct_rows=500, max_iter=1, device_loop=device_loop) as s:
         with pytest.raises(StError) as e:
             s.solve(_component(s, 6, 2))
         assert e.value.code == B.ST_ERR_NOT_CONVERGED

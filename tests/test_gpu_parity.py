@@ -338,3 +338,20 @@ def test_back_to_back_solve_combine_calls_overlap_correctly(prec):
         got = [o.cpu().numpy() for o in outs]
     for a, b in zip(got, ref):
         assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("prec,body", [(0, 4), (1, 8)])
+def test_device_side_krylov_loop_matches_the_oracle(prec, body):
+    """The inner COCG loop as one CUDA graph with a conditional WHILE node (body of
+    4 or 8 iterations, convergence tested on the device): same combined targets as the
+    oracle for multigrid components (direct limit lowered to 500 unknowns)."""
+    from paper_2606_09688_gb300 import Solver
+    p = W.layered_2d(8, 2)
+    with Solver(p, precision=prec, max_direct_rows=500, device_loop=body) as s:
+        info = s.solve(-1)
+        out = s.combine(6, 6).cpu().numpy()
+    assert info.status == 0 and info.max_inner_iters > 0
+    comps, sols = osolve.solve_all(p, method="schur")
+    pts, times = osolve.target_grid(p, 6, 6)
+    ref = osolve.combine(p, comps, sols, pts, times)
+    assert _rel(out, ref) < (TOL64 if prec == 0 else TOL32)
