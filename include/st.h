@@ -86,6 +86,16 @@ typedef struct {
   st_field u0, v0;          /* initial displacement and velocity (NULL = 0) */
   int J;                    /* combination level J >= 0 */
   int mx, mt;               /* coarsest spatial / temporal levels */
+  /* Optional nodal parametrisation (the parameters of st_misfit_gradient):
+   * c2_nodal, if not NULL, holds (2^param_level+1)^d values of c^2 at the
+   * nodes of the uniform grid of level param_level of the box (boundary
+   * included, x fastest), and c^2(x) is their multilinear interpolant (the c2
+   * callback is then not used); g_nodal likewise replaces the spatial factor g
+   * of the first source term (n_terms >= 1).  The values are copied during
+   * st_setup.  The gradient's transposed map uses the same interpolation. */
+  const double* c2_nodal;
+  const double* g_nodal;
+  int param_level;          /* 0..12; used only with c2_nodal or g_nodal */
 } st_problem;
 
 typedef struct {
@@ -210,21 +220,22 @@ st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* c
  * st_misfit_gradient: J = 1/2 sum_s w_s sum_r (u^CF(x_r, t_s) - d[s][r])^2
  * with trapezoid weights w_s on [0, T] and observations d_obs_dev (device,
  * same layout as out_dev above); its gradient with respect to
- *   - c^2 given by nodal values on the uniform grid of level jp of the box
- *     ((2^jp+1)^d nodes, x fastest) and sampled at cell centres by
- *     multilinear interpolation, into dc2_dev (device, (2^jp+1)^d doubles);
- *   - the spatial factor g of the first separable source term, given by
- *     nodal values on the same grid and interpolated multilinearly to the
- *     nodes of every component level, into dg_dev (zero if there is no
- *     source term).
+ *   - the nodal values of c^2 (st_problem.c2_nodal, required: ST_ERR_STATE
+ *     otherwise) on the uniform grid of level jp = st_problem.param_level
+ *     (ST_ERR_ARG for another jp), sampled at cell centres by multilinear
+ *     interpolation, into dc2_dev (device, (2^jp+1)^d doubles);
+ *   - the nodal values of the spatial factor g of the first separable source
+ *     term (st_problem.g_nodal, required when there is a source term),
+ *     interpolated multilinearly to the nodes of every component level, into
+ *     dg_dev (zero if there is no source term).
  * For each component k it solves the adjoint system S_k^T L_k = G_k
  * (G_k = coef_k E_k^T (w * misfit), E_k the evaluation at the receivers) with
  * the forward machinery (transposed time factors, same spatial modes, the
  * same precision and refinement as the handle), then reduces
  * dJ/dc2_e = -L_k^T (B (x) K_e) U_k per cell and dJ/dg = M_load^T sum_i b[i] L_k[i]
- * onto the parameter grid.  The caller promises that c^2 and g are the
- * multilinear interpolants of nodal fields on that grid; the library cannot
- * check it.  u0 must be zero (ST_ERR_ARG otherwise).  J_out is written on the
+ * onto the parameter grid, by the transpose of the same interpolation that
+ * st_setup used to sample the nodal fields.  u0 must be zero (ST_ERR_ARG
+ * otherwise).  J_out is written on the
  * host; info (nullable) reports the adjoint solves like st_solve_component.
  * Synchronises the handle's stream before returning. */
 st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev);

@@ -12,6 +12,7 @@
 
 #include "bspline.h"
 #include "kernels.h"
+#include "param_grid.h"
 
 namespace st {
 
@@ -1321,33 +1322,6 @@ template <typename R> __global__ void k_identity(cx<R>* __restrict__ I, int64_t 
 }
 
 // ----------------------------------------------- receiver misfit gradient
-template <int D> __device__ __forceinline__ void param_weights(const ParamGrid& pg, const double x[3], int node[8],
-                                                               double w[8]) {
-  int c[3];
-  double f[3];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const double t = (x[k] - pg.lo[k]) / pg.h[k];
-    int ci = (int)floor(t);
-    ci = ci < 0 ? 0 : (ci > pg.Np - 1 ? pg.Np - 1 : ci);
-    c[k] = ci;
-    f[k] = t - ci;
-  }
-#pragma unroll
-  for (int e = 0; e < (1 << D); ++e) {
-    double ww = 1.0;
-    int idx = 0, st = 1;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int b = (e >> k) & 1;
-      ww *= b ? f[k] : 1.0 - f[k];
-      idx += (c[k] + b) * st;
-      st *= pg.Np + 1;
-    }
-    node[e] = idx;
-    w[e] = ww;
-  }
-}
 
 __global__ void __launch_bounds__(kBlock) k_receiver_eval(const CombComp* __restrict__ comps, int ncomp,
                                                           const RecCorner* __restrict__ rc, int nrec, int ncorner,

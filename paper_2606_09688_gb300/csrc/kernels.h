@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "dsfloat.h"
+#include "param_grid.h"
 
 namespace st {
 
@@ -137,11 +138,7 @@ struct RecCorner {
   int all;
   double w;
 };
-// Uniform grid of nodal parameters on the domain box: Np cells per direction.
-struct ParamGrid {
-  int d, Np;
-  double lo[3], h[3];
-};
+// ParamGrid: the uniform grid of nodal parameters (param_grid.h).
 // Element stiffness of one cell with c^2 = 1 (2^d x 2^d, local corner c has
 // bit k set at the upper end in direction k).
 struct ElemK {

@@ -285,6 +285,8 @@ struct st_handle {
   // the count at the last st_solve_combine, sc_parity the pair buffer its
   // successor uses, sc_done_ev[p] the end of the levels of the last call that
   // used buffer p.
+  // nodal parametrisation of c^2 and of the first source term's g (copies)
+  std::vector<double> c2_nodal, g_nodal;
   int64_t api_seq = 0;
   int64_t sc_seq = -1;
   int sc_parity = 0;
@@ -463,6 +465,26 @@ st_status eval_space(st_handle* h, const st_field& f, const std::vector<double>&
   return ST_OK;
 }
 
+// Values of a nodal parameter field (level param_level, multilinear) at points.
+void eval_nodal(const st_problem& p, const std::vector<double>& vals, const std::vector<double>& pts,
+                std::vector<double>& out) {
+  ParamGrid pg{};
+  pg.d = p.d;
+  pg.Np = 1 << p.param_level;
+  for (int k = 0; k < p.d; ++k) {
+    pg.lo[k] = p.lo[k];
+    pg.h[k] = (p.hi[k] - p.lo[k]) / pg.Np;
+  }
+  const int64_t n = (int64_t)pts.size() / p.d;
+  out.assign(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < p.d; ++k) x[k] = pts[(size_t)i * p.d + k];
+    out[i] = p.d == 1 ? param_eval<1>(pg, vals.data(), x)
+                      : (p.d == 2 ? param_eval<2>(pg, vals.data(), x) : param_eval<3>(pg, vals.data(), x));
+  }
+}
+
 std::vector<double> node_points(const st_problem& p, int j) {
   const int N = 1 << j, d = p.d;
   int64_t nn = 1;
@@ -581,7 +603,9 @@ st_status setup_space_level(st_handle* h, int jx, SpaceLevel& sl) {
   sl.geo = make_geo(p.d, jx);
   for (int k = 0; k < p.d; ++k) sl.h[k] = (p.hi[k] - p.lo[k]) / (1 << jx);
   sl.sc = make_coef(p.d, sl.h);
-  st_status s = eval_space(h, p.c2, cell_centres(p, jx), p.d, sl.c2h);
+  st_status s = ST_OK;
+  if (!h->c2_nodal.empty()) eval_nodal(p, h->c2_nodal, cell_centres(p, jx), sl.c2h);
+  else s = eval_space(h, p.c2, cell_centres(p, jx), p.d, sl.c2h);
   if (s != ST_OK) return s;
   sl.c2min = 1e300;
   for (double v : sl.c2h) {
@@ -601,9 +625,14 @@ st_status setup_space_level(st_handle* h, int jx, SpaceLevel& sl) {
   double* tmp = h->alloc<double>((size_t)sl.nall);
   ST_NEED(h, tmp);
   std::vector<double> vals;
-  auto load_row = [&](const st_field& f, int row, double aK, double aM, bool keep_lift) -> st_status {
-    st_status s2 = eval_space(h, f, pts, p.d, vals);
-    if (s2 != ST_OK) return s2;
+  auto load_row = [&](const st_field& f, int row, double aK, double aM, bool keep_lift,
+                      const std::vector<double>* nodal = nullptr) -> st_status {
+    if (nodal != nullptr && !nodal->empty()) {
+      eval_nodal(p, *nodal, pts, vals);
+    } else {
+      st_status s2 = eval_space(h, f, pts, p.d, vals);
+      if (s2 != ST_OK) return s2;
+    }
     ST_CUDA(h, cudaMemcpyAsync(tmp, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->h2d_bytes += (int64_t)(vals.size() * sizeof(double));
     launch_load(sl.geo, sl.sc, sl.c2d, tmp, sl.loads + (size_t)row * sl.geo.nnodes, aK, aM, 0, h->stream);
@@ -617,7 +646,7 @@ st_status setup_space_level(st_handle* h, int jx, SpaceLevel& sl) {
   };
   for (int r = 0; r < p.n_terms; ++r) {
     st_field g{p.terms[r].g, p.terms[r].g_user};
-    if ((s = load_row(g, r, 0.0, 1.0, false)) != ST_OK) return s;
+    if ((s = load_row(g, r, 0.0, 1.0, false, r == 0 ? &h->g_nodal : nullptr)) != ST_OK) return s;
   }
   if ((s = load_row(p.v0, p.n_terms, 0.0, 1.0, false)) != ST_OK) return s;
   if ((s = load_row(p.u0, p.n_terms + 1, 1.0, 0.0, true)) != ST_OK) return s;
@@ -1895,7 +1924,10 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   for (int k = 0; k < p.d; ++k)
     if (!(p.hi[k] > p.lo[k])) return fail(nullptr, ST_ERR_ARG, "empty box");
   if (p.J < 0 || p.mx < 1 || p.mt < 0) return fail(nullptr, ST_ERR_ARG, "levels: need J >= 0, mx >= 1, mt >= 0");
-  if (p.c2.fn == nullptr) return fail(nullptr, ST_ERR_ARG, "c^2 callback is required");
+  if (p.c2.fn == nullptr && p.c2_nodal == nullptr) return fail(nullptr, ST_ERR_ARG, "c^2 callback or nodal values required");
+  if ((p.c2_nodal != nullptr || p.g_nodal != nullptr) && (p.param_level < 0 || p.param_level > 12))
+    return fail(nullptr, ST_ERR_ARG, "param_level must be 0..12");
+  if (p.g_nodal != nullptr && p.n_terms < 1) return fail(nullptr, ST_ERR_ARG, "g_nodal needs a source term");
   if (p.n_terms < 0 || (p.n_terms > 0 && p.terms == nullptr)) return fail(nullptr, ST_ERR_ARG, "bad source terms");
   const int jx_max = p.mx + p.J, jt_max = p.mt + p.J;
   const int cap = p.d == 1 ? 20 : (p.d == 2 ? 13 : 9);
@@ -1903,6 +1935,14 @@ st_status st_setup(const st_problem* problem, const st_options* options, st_hand
   auto h = std::make_unique<st_handle>();
   h->prob = p;
   if (options) h->opt = *options;
+  if (p.c2_nodal != nullptr || p.g_nodal != nullptr) {
+    int64_t np = 1;
+    for (int k = 0; k < p.d; ++k) np *= (1 << p.param_level) + 1;
+    if (p.c2_nodal != nullptr) h->c2_nodal.assign(p.c2_nodal, p.c2_nodal + np);
+    if (p.g_nodal != nullptr) h->g_nodal.assign(p.g_nodal, p.g_nodal + np);
+  }
+  h->prob.c2_nodal = nullptr;  // the copies above are used from here on
+  h->prob.g_nodal = nullptr;
   if (h->opt.precision != ST_FP64 && h->opt.precision != ST_FP32_IR)
     return fail(nullptr, ST_ERR_ARG, "unknown precision");
   if (!(h->opt.inner_tol >= 0.0 && h->opt.inner_tol < 1.0) || !(h->opt.tol >= 0.0 && h->opt.tol < 1.0))
@@ -2324,6 +2364,9 @@ st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int
   const st_problem& p = h->prob;
   if (jt_star < 0 || jt_star > 14 || jp < 0 || jp > 12) return fail(h, ST_ERR_ARG, "bad level");
   if (p.u0.fn != nullptr) return fail(h, ST_ERR_ARG, "the c^2 gradient is implemented for u0 = 0 only");
+  if (h->c2_nodal.empty() || (p.n_terms > 0 && h->g_nodal.empty()))
+    return fail(h, ST_ERR_STATE, "the gradient is taken with respect to nodal c^2 and g: set c2_nodal (and g_nodal)");
+  if (jp != p.param_level) return fail(h, ST_ERR_ARG, "jp differs from the problem's param_level");
   for (auto& c : h->comps)
     if (!c->solved) return fail(h, ST_ERR_STATE, "gradient before every component is solved");
   st_status s = build_receivers(h, jt_star, x_rec, n_rec);

@@ -38,7 +38,8 @@ class StProblem(C.Structure):
     _fields_ = [("d", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("T", C.c_double),
                 ("c2", StField), ("n_terms", C.c_int), ("terms", C.POINTER(StSourceTerm)),
                 ("f_general", SPACETIME_FN), ("f_user", C.c_void_p), ("u0", StField), ("v0", StField),
-                ("J", C.c_int), ("mx", C.c_int), ("mt", C.c_int)]
+                ("J", C.c_int), ("mx", C.c_int), ("mt", C.c_int),
+                ("c2_nodal", C.c_void_p), ("g_nodal", C.c_void_p), ("param_level", C.c_int)]
 
 
 class StOptions(C.Structure):
@@ -155,12 +156,15 @@ class Solver:
     def __init__(self, problem, precision: int = ST_FP64, tol: float = 0.0, max_iter: int = 0,
                  max_sweeps: int = 0, stream=None, inner_tol: float = 0.0, max_direct_rows: int = 0,
                  autotune: int = 0, mem_cap_bytes: int = 0, wait_cycles: int = 0, inject_stall: int = 0,
-                 device_loop: int = 0):
+                 device_loop: int = 0, c2_nodal=None, g_nodal=None, param_level: int = 0):
+        """c2_nodal / g_nodal: optional nodal values ((2^param_level+1)^d, x fastest) of
+        c^2 and of the first source term's spatial factor on the uniform grid of level
+        param_level; the library interpolates them (and its gradient uses the transpose)."""
         import torch
         self._lib = lib()
         p = problem
         d = p.d
-        keep = []  # callbacks must outlive st_setup
+        keep = []  # callbacks and arrays must outlive st_setup
 
         def field(fn):
             if fn is None:
@@ -171,7 +175,8 @@ class Solver:
 
         terms = (StSourceTerm * max(1, len(p.terms)))()
         for r, (g, s) in enumerate(p.terms):
-            gc, sc = _space_cb(g, d), _time_cb(s)
+            gc = SPACE_FN() if g is None else _space_cb(g, d)
+            sc = _time_cb(s)
             keep += [gc, sc]
             terms[r] = StSourceTerm(gc, None, sc, None)
         prob = StProblem()
@@ -190,6 +195,14 @@ class Solver:
         prob.u0 = field(p.u0)
         prob.v0 = field(p.v0)
         prob.J, prob.mx, prob.mt = p.J, p.mx, p.mt
+        for name, arr in (("c2_nodal", c2_nodal), ("g_nodal", g_nodal)):
+            if arr is not None:
+                a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).ravel())
+                if a.size != ((1 << param_level) + 1) ** d:
+                    raise ValueError(f"{name}: expected {((1 << param_level) + 1) ** d} nodal values")
+                keep.append(a)
+                setattr(prob, name, a.ctypes.data)
+        prob.param_level = param_level
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -6,6 +6,8 @@ J along 20 seeded directions on the differentiation configuration (d = 2,
 n = 10, m = 2, 65 x 65 nodal c^2 and g, 32 receivers on y = 0.9), the
 FP32 + refinement path against the FP64 path, and the autograd wrapper.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -35,13 +37,12 @@ def _oracle_obs(st):
 @pytest.mark.parametrize("n,m,jp,nrec", [(4, 1, 2, 5), (6, 1, 3, 8), (7, 2, 4, 12)])
 def test_misfit_and_gradient_match_the_oracle(n, m, jp, nrec):
     import torch
-    from paper_2606_09688_gb300 import ST_FP64, Solver
-    from paper_2606_09688_gb300.adjoint import problem_with
+    from paper_2606_09688_gb300 import ST_FP64
+    from paper_2606_09688_gb300.adjoint import nodal_solver
     st = W.inverse_2d(n=n, m=m, jp=jp, n_receivers=nrec, seed=n)
     d_obs = _oracle_obs(st)
     J0, gc0, gg0 = OA.gradient(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp, st.receivers, st.jt_star, d_obs)
-    p = problem_with(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp)
-    with Solver(p, precision=ST_FP64) as s:
+    with nodal_solver(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp, ST_FP64) as s:
         s.solve(-1)
         vals = s.receiver_values(st.jt_star, st.receivers).cpu().numpy()
         J, gc, gg, info = s.misfit_gradient(st.jt_star, st.receivers, torch.from_numpy(d_obs).cuda(), st.jp)
@@ -66,13 +67,12 @@ def _diff_setup():
 
 
 def test_gradient_matches_central_differences_on_20_directions():
-    from paper_2606_09688_gb300 import ST_FP64, Solver
-    from paper_2606_09688_gb300.adjoint import problem_with
+    from paper_2606_09688_gb300 import ST_FP64
+    from paper_2606_09688_gb300.adjoint import nodal_solver
     st, d_obs = _diff_setup()
 
     def J_and_grad(c2, g, grad=False):
-        p = problem_with(st.base, c2, g, st.s, st.jp)
-        with Solver(p, precision=ST_FP64) as s:
+        with nodal_solver(st.base, c2, g, st.s, st.jp, ST_FP64) as s:
             s.solve(-1)
             J, gc, gg, _ = s.misfit_gradient(st.jt_star, st.receivers, d_obs, st.jp)
         return (J, gc.cpu().numpy(), gg.cpu().numpy()) if grad else J
@@ -98,13 +98,12 @@ def test_gradient_matches_central_differences_on_20_directions():
 
 
 def test_fp32_refinement_gradient_matches_fp64():
-    from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64, Solver
-    from paper_2606_09688_gb300.adjoint import problem_with
+    from paper_2606_09688_gb300 import ST_FP32_IR, ST_FP64
+    from paper_2606_09688_gb300.adjoint import nodal_solver
     st, d_obs = _diff_setup()
     out = {}
     for prec in (ST_FP64, ST_FP32_IR):
-        p = problem_with(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp)
-        with Solver(p, precision=prec) as s:
+        with nodal_solver(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp, prec) as s:
             s.solve(-1)
             out[prec] = s.misfit_gradient(st.jt_star, st.receivers, d_obs, st.jp)
     J64, gc64, gg64, _ = out[ST_FP64]
@@ -136,10 +135,9 @@ def test_misfit_gradient_argument_errors():
     from paper_2606_09688_gb300 import Solver, StError
     from paper_2606_09688_gb300 import st as B
     st = W.inverse_2d(n=4, m=1, jp=2, n_receivers=3)
-    from paper_2606_09688_gb300.adjoint import problem_with
-    p = problem_with(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp)
+    from paper_2606_09688_gb300.adjoint import nodal_solver, problem_with
     d = torch.zeros(((1 << st.jt_star) + 1, 3), dtype=torch.float64, device="cuda")
-    with Solver(p) as s:
+    with nodal_solver(st.base, st.c2_nodal, st.g_nodal, st.s, st.jp) as s:
         with pytest.raises(StError) as e:
             s.misfit_gradient(st.jt_star, st.receivers, d, st.jp)
         assert e.value.code == B.ST_ERR_STATE                 # not solved yet
@@ -147,6 +145,16 @@ def test_misfit_gradient_argument_errors():
         with pytest.raises(StError) as e:
             s.misfit_gradient(st.jt_star, st.receivers + 2.0, d, st.jp)
         assert e.value.code == B.ST_ERR_ARG                   # receivers outside the box
+        with pytest.raises(StError) as e:
+            s.misfit_gradient(st.jt_star, st.receivers, d, st.jp + 1)
+        assert e.value.code == B.ST_ERR_ARG                   # another parameter level than the problem's
+    # c^2 from a callback: the gradient with respect to nodal values is refused
+    with Solver(dataclasses.replace(problem_with(st.base, st.s), c2=st.base.c2, terms=st.base.terms or
+                                    [(lambda x: np.ones(len(x)), st.s)])) as s:
+        s.solve(-1)
+        with pytest.raises(StError) as e:
+            s.misfit_gradient(st.jt_star, st.receivers, d, st.jp)
+        assert e.value.code == B.ST_ERR_STATE
     q = W.standing_wave(2, 4, 1)                              # u0 != 0
     with Solver(q) as s:
         s.solve(-1)
