@@ -133,3 +133,35 @@ def interpolate_nodal(values_all, d, lo, hi, jx, pts):
             stride *= nn
         vals += w * values_all[g]
     return vals
+
+
+def interpolate_nodal_grad(values_all, d, lo, hi, jx, pts):
+    """Gradient (n, d) at the points of the Q1 function with the given values on all
+    (N+1)^d nodes: the derivative of the multilinear interpolant in each direction
+    (inside the cell holding the point)."""
+    N, h = grid(d, lo, hi, jx)
+    nn = N + 1
+    idx, frac = [], []
+    for k in range(d):
+        s = (pts[:, k] - lo[k]) / h[k]
+        c = np.clip(np.floor(s).astype(np.int64), 0, N - 1)
+        idx.append(c)
+        frac.append(s - c)
+    g = np.zeros((len(pts), d))
+    for c in range(1 << d):
+        node = np.zeros(len(pts), dtype=np.int64)
+        stride = 1
+        for k in range(d):
+            node += (idx[k] + ((c >> k) & 1)) * stride
+            stride *= nn
+        v = values_all[node]
+        for k in range(d):
+            w = np.ones(len(pts))
+            for l in range(d):
+                b = (c >> l) & 1
+                if l == k:
+                    w *= (1.0 if b else -1.0) / h[k]
+                else:
+                    w *= frac[l] if b else (1.0 - frac[l])
+            g[:, k] += w * v
+    return g

@@ -132,6 +132,34 @@ def e2_variable_speed(J: int) -> Problem:
                    J=J, mx=1, mt=1, name="e2_variable_speed")
 
 
+def travelling_wave(J: int, h0_level: int = 1) -> Problem:
+    """Section 6.3: Omega = (-1,1), T = 1, c = 4/5, f = 0,
+    u = w(x - ct) - w(2 - x - ct) with w(s) = exp(-16 (s - 0.6)^2): a pulse moving
+    right and reflecting off x = 1 (u(1, t) = 0 exactly; |u(-1, t)| <= 1e-17).
+    u0 = w(x) - w(2 - x), v0 = -c w'(x) + c w'(2 - x).  Coarsest mesh h0 = 2^-h0_level
+    relative to the interval length 2 in space and to T in time (levels mx = h0_level + 1,
+    mt = h0_level)."""
+    c = 0.8
+
+    def w(sv):
+        return np.exp(-16.0 * (sv - 0.6) ** 2)
+
+    def dw(sv):
+        return -32.0 * (sv - 0.6) * w(sv)
+
+    def exact(x, t):
+        x = x[:, 0]
+        return w(x - c * t) - w(2.0 - x - c * t)
+
+    p = Problem(d=1, lo=(-1.0,), hi=(1.0,), T=1.0, c2=lambda x: np.full(len(x), c * c),
+                u0=lambda x: w(x[:, 0]) - w(2.0 - x[:, 0]),
+                v0=lambda x: -c * dw(x[:, 0]) + c * dw(2.0 - x[:, 0]),
+                exact=exact, J=J, mx=h0_level + 1, mt=h0_level, name=f"travelling_wave_J{J}")
+    p.exact_dt = lambda x, t: -c * dw(x[:, 0] - c * t) + c * dw(2.0 - x[:, 0] - c * t)
+    p.exact_grad = lambda x, t: (dw(x[:, 0] - c * t) + dw(2.0 - x[:, 0] - c * t))[:, None]
+    return p
+
+
 # ------------------------------------------------------- workload recipes
 def ricker(fp: float = 8.0, t0: Optional[float] = None) -> TimeFn:
     """Ricker wavelet (1 - 2 pi^2 fp^2 (t-t0)^2) exp(-pi^2 fp^2 (t-t0)^2), t0 = 1/fp."""
