@@ -242,6 +242,19 @@ st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int
 st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int n_rec, const double* d_obs_dev,
                              int jp, double* J_out, double* dc2_dev, double* dg_dev, st_solve_info* info);
 
+/* Energy of the combined solution, Section 6.3:
+ *   E(t_i; u^CF) = 1/2 ( ||d_t u^CF(., t_i)||^2_{L^2} + ||c grad u^CF(., t_i)||^2_{L^2} )
+ * at the ntimes times t_i in [0, T] (host array), written to energy_out (host,
+ * ntimes doubles).  u^CF and d_t u^CF are formed on all nodes of the uniform
+ * grid of spatial level jx_eval (0 = the finest component level, the only
+ * other value accepted), where the combined solution is Q1 in space, and the
+ * integrals are taken exactly per cell with c^2 cellwise at that level's cell
+ * centres.  Requires every component solved (ST_ERR_STATE); ST_ERR_ARG for
+ * times outside [0, T] or another jx_eval; device memory for the levels and
+ * tables is taken with cudaMallocAsync on the handle's stream (ST_ERR_OOM if
+ * that fails).  Synchronises the handle's stream. */
+st_status st_energy(st_handle* h, const double* times, int ntimes, int jx_eval, double* energy_out);
+
 /* Copy the FP64 coefficient array U_k (n_time x n_space, time-major) of a
  * solved component to caller-owned host memory. */
 st_status st_component_coeffs(st_handle* h, int k, double* host_out);

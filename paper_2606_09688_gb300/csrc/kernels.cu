@@ -1647,6 +1647,77 @@ void launch_gemm_right(const double* X, const double* Phi, double* Y, int nt, in
   k_gemm_right<<<grid, block, 0, s>>>(X, Phi, Y, nt, nx, accumulate);
 }
 
+// Energy of Section 6.3 on the cells of one level: for every time b,
+// part[b][block] = 1/2 sum over the block's cells e of
+//   z_e^T Me z_e + c2_e y_e^T Ke y_e,
+// y (values) and z (time derivatives) on all (N+1)^D nodes of the level (x
+// fastest), Me / Ke the element mass and unit-coefficient stiffness (local
+// corner c: bit k set at the upper end in direction k), c2 cellwise.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_energy_cells(int N, const double* __restrict__ c2,
+                                                         const double* __restrict__ y, const double* __restrict__ z,
+                                                         int64_t nall, ElemK me, ElemK ke, double* __restrict__ part) {
+  constexpr int NC = 1 << D;
+  const int b = blockIdx.y;
+  int64_t ncell = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) ncell *= N;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (e < ncell) {
+    int64_t r = e, base = 0, st = 1;
+    int64_t off[NC];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int64_t ik = r % N;
+      r /= N;
+      base += ik * st;
+      st *= (N + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      int64_t o = 0, s2 = 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        o += ((c >> k) & 1) * s2;
+        s2 *= (N + 1);
+      }
+      off[c] = base + o;
+    }
+    double yv[NC], zv[NC];
+    const double* yb = y + (int64_t)b * nall;
+    const double* zb = z + (int64_t)b * nall;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      yv[c] = yb[off[c]];
+      zv[c] = zb[off[c]];
+    }
+    double qm = 0.0, qk = 0.0;
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+      double rm = 0.0, rk = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        rm = fma(me.k[a * NC + c], zv[c], rm);
+        rk = fma(ke.k[a * NC + c], yv[c], rk);
+      }
+      qm = fma(zv[a], rm, qm);
+      qk = fma(yv[a], rk, qk);
+    }
+    acc = 0.5 * (qm + c2[e] * qk);
+  }
+  const cx<double> t = block_sum(mk<double>(acc, 0.0));
+  if (threadIdx.x == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = t.re;
+}
+
+__global__ void k_energy_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  const int b = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[(int64_t)b * nblk + i];
+  const cx<double> t = block_sum(mk<double>(acc, 0.0));
+  if (threadIdx.x == 0) out[b] = t.re;
+}
+
 // Condition of the device-side COCG loop (a WHILE node of a CUDA graph):
 // continue while any mode is still iterating.  Every mode leaves the active
 // set at convergence, at a breakdown or at its iteration limit, so the loop
@@ -1657,6 +1728,19 @@ __global__ void k_cocg_continue(const CocgScal* __restrict__ scal, int nmodes, c
   for (int q = threadIdx.x; q < nmodes; q += blockDim.x) any |= scal[q].active;
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+void launch_energy_cells(int d, int N, const double* c2, const double* y, const double* z, int64_t nall, int ntimes,
+                         const ElemK& me, const ElemK& ke, double* part, double* out, cudaStream_t s) {
+  int64_t ncell = 1;
+  for (int k = 0; k < d; ++k) ncell *= N;
+  const unsigned nblk = blocks_for(ncell);
+  const dim3 grid(nblk, ntimes);
+  if (d == 1) k_energy_cells<1><<<grid, kBlock, 0, s>>>(N, c2, y, z, nall, me, ke, part);
+  else if (d == 2) k_energy_cells<2><<<grid, kBlock, 0, s>>>(N, c2, y, z, nall, me, ke, part);
+  else k_energy_cells<3><<<grid, kBlock, 0, s>>>(N, c2, y, z, nall, me, ke, part);
+  k_energy_final<<<ntimes, kBlock, 0, s>>>(part, (int)nblk, out);
+  count(2);
 }
 
 void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, cudaStream_t s) {

@@ -161,6 +161,12 @@ void launch_grad_c2(const Geo& g, const double* lo, int nt, const double* Bband,
 void launch_grad_g(const Geo& g, const double* lo, const StencilCoef& sc, int nt, const double* b, const double* L,
                    double* v, const ParamGrid& pg, double* dg, cudaStream_t s);
 
+// Energy of Section 6.3 per time: out[b] = 1/2 sum_e (z_e^T Me z_e + c2_e y_e^T Ke y_e) over
+// the N^d cells of a level (y, z on all (N+1)^d nodes, ntimes rows of nall); part:
+// scratch of ntimes x ceil(N^d / 256) doubles.
+void launch_energy_cells(int d, int N, const double* c2, const double* y, const double* z, int64_t nall, int ntimes,
+                         const ElemK& me, const ElemK& ke, double* part, double* out, cudaStream_t s);
+
 // Stencil autotuner: times the launch shapes of one stencil operation on the
 // given buffers (synchronises the stream) and keeps the fastest for later
 // launch_stencil calls with the same operation, dimension, precision, grid

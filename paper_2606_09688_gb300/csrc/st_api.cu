@@ -1671,6 +1671,19 @@ ElemK element_stiffness(int d, const double* h) {
   return ke;
 }
 
+// Q1 element mass on a cell of widths h: the tensor product of the 1D masses h/6 [[2,1],[1,2]].
+ElemK element_mass(int d, const double* h) {
+  ElemK me{};
+  const int nc = 1 << d;
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b < nc; ++b) {
+      double m = 1.0;
+      for (int l = 0; l < d; ++l) m *= h[l] / 6.0 * ((((a >> l) & 1) == ((b >> l) & 1)) ? 2.0 : 1.0);
+      me.k[a * nc + b] = m;
+    }
+  return me;
+}
+
 // Combination tables for a target level pair and a component set (bit mask):
 // components sorted by their combination level min(jx, jx*), B-spline values
 // of every component at every target time, partial-sum buffers per level.
@@ -2428,6 +2441,121 @@ st_status st_tuned_shapes(int* out, int max_entries, int* n_out) {
   if (!n_out || max_entries < 0) return ST_ERR_ARG;
   *n_out = tuned_stencil_shapes(out, max_entries);
   return ST_OK;
+}
+
+st_status st_energy(st_handle* h, const double* times, int ntimes, int jx_eval, double* energy_out) {
+  if (!h || !times || !energy_out || ntimes < 1) return ST_ERR_ARG;
+  ++h->api_seq;
+  const st_problem& p = h->prob;
+  const int nc = (int)h->comps.size();
+  int jmax = 0;
+  for (auto& c : h->comps) {
+    if (!c->solved) return fail(h, ST_ERR_STATE, "energy before every component is solved");
+    jmax = std::max(jmax, c->jx);
+  }
+  if (jx_eval == 0) jx_eval = jmax;
+  if (jx_eval != jmax) return fail(h, ST_ERR_ARG, "jx_eval must be 0 or the finest spatial level of the components");
+  for (int i = 0; i < ntimes; ++i)
+    if (!(times[i] >= 0.0 && times[i] <= p.T)) return fail(h, ST_ERR_ARG, "times must lie in [0, T]");
+  const SpaceLevel& sl = *h->space[jx_eval];
+  const int d = p.d, N = 1 << jx_eval;
+  int64_t nall = 1, ncell = 1;
+  for (int k = 0; k < d; ++k) {
+    nall *= N + 1;
+    ncell *= N;
+  }
+  // components in level order; the combination levels evaluate u^CF and d_t u^CF
+  // on all nodes of level jx_eval at a batch of times
+  std::vector<int> order(nc);
+  for (int c = 0; c < nc; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->comps[a]->jx < h->comps[b]->jx; });
+  const int jmin = h->comps[order[0]]->jx;
+  std::vector<int> first(jx_eval + 2, nc);
+  for (int o = nc - 1; o >= 0; --o) first[h->comps[order[o]]->jx] = o;
+  for (int lev = jx_eval; lev >= 0; --lev) first[lev] = std::min(first[lev], first[lev + 1]);
+  std::vector<CombComp> cv(nc), cd(nc);
+  for (int o = 0; o < nc; ++o) {
+    const Component& k = *h->comps[order[o]];
+    cv[o] = CombComp{k.U, k.sl->lift, k.jx, k.jt, k.coef, 0};
+    cd[o] = CombComp{k.U, nullptr, k.jx, k.jt, k.coef, 0};
+  }
+  const int64_t budget = (int64_t)256 << 20;  // device bytes for the level arrays of one batch
+  const int B = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)ntimes, 256, budget / (nall * 8 * 4)}));
+  const unsigned nblk = (unsigned)((ncell + 255) / 256);
+  cudaStream_t st = h->stream;
+  // call-local device memory, stream-ordered
+  std::vector<void*> bufs;
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMallocAsync(&q, bytes, st) != cudaSuccess) return nullptr;
+    bufs.push_back(q);
+    return q;
+  };
+  auto release = [&]() {
+    for (void* q : bufs) cudaFreeAsync(q, st);
+    bufs.clear();
+  };
+  CombComp* dcv = (CombComp*)dalloc(sizeof(CombComp) * nc);
+  CombComp* dcd = (CombComp*)dalloc(sizeof(CombComp) * nc);
+  double* tbv = (double*)dalloc(sizeof(double) * 3 * nc * B);
+  double* tbd = (double*)dalloc(sizeof(double) * 3 * nc * B);
+  int* tsp = (int*)dalloc(sizeof(int) * nc * B);
+  double* part = (double*)dalloc(sizeof(double) * (size_t)nblk * B);
+  double* eout = (double*)dalloc(sizeof(double) * ntimes);
+  std::vector<double*> Yv(jx_eval + 1, nullptr), Yd(jx_eval + 1, nullptr);
+  bool ok = dcv && dcd && tbv && tbd && tsp && part && eout;
+  for (int lev = jmin; lev <= jx_eval && ok; ++lev) {
+    int64_t nsp = 1;
+    for (int k = 0; k < d; ++k) nsp *= (1 << lev) + 1;
+    Yv[lev] = (double*)dalloc(sizeof(double) * nsp * B);
+    Yd[lev] = (double*)dalloc(sizeof(double) * nsp * B);
+    ok = Yv[lev] && Yd[lev];
+  }
+  if (!ok) {
+    cudaGetLastError();
+    release();
+    return fail(h, ST_ERR_OOM, "device allocation failed");
+  }
+  ST_CUDA(h, cudaMemcpyAsync(dcv, cv.data(), sizeof(CombComp) * nc, cudaMemcpyHostToDevice, st));
+  ST_CUDA(h, cudaMemcpyAsync(dcd, cd.data(), sizeof(CombComp) * nc, cudaMemcpyHostToDevice, st));
+  const ElemK me = element_mass(d, sl.h), ke = element_stiffness(d, sl.h);
+  std::vector<double> hv((size_t)3 * nc * B), hd((size_t)3 * nc * B);
+  std::vector<int> hs((size_t)nc * B);
+  for (int t0 = 0; t0 < ntimes; t0 += B) {
+    const int nb = std::min(B, ntimes - t0);
+    for (int o = 0; o < nc; ++o) {
+      const Component& k = *h->comps[order[o]];
+      const int Nt = 1 << k.jt;
+      for (int b = 0; b < nb; ++b) {
+        const double t = times[t0 + b];
+        const int span = std::min(Nt - 1, std::max(0, (int)std::floor(t * Nt / p.T)));
+        double v[3], d1[3], d2[3];
+        bspline_local(Nt, p.T, span, t, v, d1, d2);
+        for (int a = 0; a < 3; ++a) {
+          hv[((size_t)o * nb + b) * 3 + a] = v[a];
+          hd[((size_t)o * nb + b) * 3 + a] = d1[a];
+        }
+        hs[(size_t)o * nb + b] = span;
+      }
+    }
+    ST_CUDA(h, cudaMemcpyAsync(tbv, hv.data(), sizeof(double) * 3 * nc * nb, cudaMemcpyHostToDevice, st));
+    ST_CUDA(h, cudaMemcpyAsync(tbd, hd.data(), sizeof(double) * 3 * nc * nb, cudaMemcpyHostToDevice, st));
+    ST_CUDA(h, cudaMemcpyAsync(tsp, hs.data(), sizeof(int) * nc * nb, cudaMemcpyHostToDevice, st));
+    for (int lev = jmin; lev <= jx_eval; ++lev) {
+      const double* pv = lev > jmin ? Yv[lev - 1] : nullptr;
+      const double* pd = lev > jmin ? Yd[lev - 1] : nullptr;
+      launch_comb_level(d, lev, pv, dcv, first[lev], first[lev + 1], tbv, tsp, nb, Yv[lev], st);
+      launch_comb_level(d, lev, pd, dcd, first[lev], first[lev + 1], tbd, tsp, nb, Yd[lev], st);
+    }
+    launch_energy_cells(d, N, sl.c2d, Yv[jx_eval], Yd[jx_eval], nall, nb, me, ke, part, eout + t0, st);
+    // the host tables are overwritten by the next batch: wait for this batch's copies
+    ST_CUDA(h, cudaStreamSynchronize(st));
+  }
+  ST_CUDA(h, cudaMemcpyAsync(energy_out, eout, sizeof(double) * ntimes, cudaMemcpyDeviceToHost, st));
+  release();
+  ST_CUDA(h, cudaStreamSynchronize(st));
+  h->d2h_bytes += (int64_t)(sizeof(double) * ntimes);
+  return check_launch(h, "energy");
 }
 
 st_status st_component_coeffs(st_handle* h, int k, double* host_out) {

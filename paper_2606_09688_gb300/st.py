@@ -325,6 +325,16 @@ class Solver:
                                                   C.byref(info)))
         return J.value, dc2, dg, info
 
+    def energy(self, times, jx_eval: int = 0) -> np.ndarray:
+        """E(t; u^CF) of Section 6.3 at the given times in [0, T] (st_energy)."""
+        t = np.ascontiguousarray(np.asarray(times, dtype=np.float64).ravel())
+        out = np.empty(len(t))
+        self._lib.st_energy.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        self._lib.st_energy.restype = C.c_int
+        self._check(self._lib.st_energy(self._h, t.ctypes.data_as(C.c_void_p), len(t), jx_eval,
+                                        out.ctypes.data_as(C.c_void_p)))
+        return out
+
     def coeffs(self, k: int) -> np.ndarray:
         info = self.component(k)
         out = np.empty((info.n_time, info.n_space), dtype=np.float64)
