@@ -84,3 +84,26 @@ def test_energy_argument_errors():
         with pytest.raises(StError) as e:
             s.energy([0.5], jx_eval=2)
         assert e.value.code == B.ST_ERR_ARG
+
+
+def test_coarsest_mesh_study_of_section_6_3():
+    """Section 6.3, h0 study: three sequences with coarsest meshes h0 = 2^-1, 2^-2, 2^-3 and
+    the same finest meshes.  For the travelling wave, the relative L^2(Q_T) error of the
+    GPU's combined solution (the oracle's quadrature applied to the GPU's component
+    arrays) decreases at every finest mesh as h0 is refined, and with h0 = 2^-3 it
+    converges at the O(h^2) rate of Theorem 1 (error ratio near 4 per level)."""
+    from paper_2606_09688_gb300 import ST_FP64, Solver
+    errs = {}
+    for h0 in (1, 2, 3):
+        for finest in (4, 5, 6):
+            J = finest - h0
+            p = W.travelling_wave(J, h0_level=h0)
+            with Solver(p, precision=ST_FP64) as s:
+                s.solve(-1)
+                infos = s.components()
+                sols = [s.coeffs(k) for k in range(len(infos))]
+            comps = [(ci.jx, ci.jt, ci.coef) for ci in infos]
+            errs[(h0, finest)] = osolve.l2_error_qt(p, comps, sols, p.mx + p.J, p.mt + p.J)
+    for finest in (4, 5, 6):
+        assert errs[(3, finest)] < errs[(2, finest)] < errs[(1, finest)], errs
+    assert 3.0 < errs[(3, 5)] / errs[(3, 6)] < 5.0, errs
