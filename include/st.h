@@ -129,13 +129,20 @@ typedef struct {
                            never issued, so its bounded wait runs out after
                            wait_cycles and the solve returns ST_ERR_TIMEOUT;
                            0 = off (default) */
-  int device_loop;      /* inner Krylov loop of the multigrid components:
-                           0 = graph launches of 4 iterations with a host check
-                           of convergence after each (default); k = 4, 8 or 16 =
-                           the whole loop on the device as one CUDA graph with a
-                           conditional WHILE node whose body runs k iterations
-                           and tests convergence on the device (no host round
-                           trip until the refinement sweep's norms) */
+  int device_loop;      /* 0 = host-driven solves (default): the refinement
+                           sweeps and, for multigrid components, graph launches
+                           of 4 COCG iterations with a host check of
+                           convergence after each; k = 4, 8 or 16 = every
+                           forward solve is one CUDA graph launch: the sweeps
+                           run in a conditional WHILE node whose stopping test
+                           (the backward error, the sweep limit, status words)
+                           is taken on the device, and each sweep's COCG loop
+                           in a nested WHILE node of k iterations per test.
+                           st_solve_component, st_solve_batch and
+                           st_solve_combine then enqueue every component from
+                           the calling thread and synchronise once per call to
+                           read the solves' records (st_solve_combine: before
+                           its last combination levels end) */
 } st_options;
 
 typedef struct {

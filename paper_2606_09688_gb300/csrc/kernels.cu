@@ -1723,11 +1723,60 @@ __global__ void k_energy_final(const double* __restrict__ part, int nblk, double
 // set at convergence, at a breakdown or at its iteration limit, so the loop
 // ends after at most max_iter / (iterations per body) + 1 bodies.  One thread
 // sets the condition (concurrent calls would race).
-__global__ void k_cocg_continue(const CocgScal* __restrict__ scal, int nmodes, cudaGraphConditionalHandle handle) {
+__global__ void k_cocg_continue(const CocgScal* __restrict__ scal, int nmodes, cudaGraphConditionalHandle handle,
+                                int* bodies) {
   int any = 0;
   for (int q = threadIdx.x; q < nmodes; q += blockDim.x) any |= scal[q].active;
   any = __syncthreads_or(any);
-  if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    if (bodies != nullptr) ++*bodies;
+    cudaGraphSetConditional(handle, any ? 1u : 0u);
+  }
+}
+
+__global__ void k_refine_init(RefineRec* __restrict__ rec, const double* __restrict__ fn2,
+                              cudaGraphConditionalHandle h) {
+  const double f = fn2[0];
+  RefineRec r{};
+  r.eta_prev = 1e300;
+  r.status = (f >= 0.0 && f <= 1.7e308) ? RR_OK : RR_NUMERIC;
+  *rec = r;
+  cudaGraphSetConditional(h, (r.status == RR_OK && f > 0.0) ? 1u : 0u);
+}
+
+// The refinement test of one sweep, as the host loop takes it (one warp).
+__global__ void k_refine_decide(RefineRec* __restrict__ rec, const double* __restrict__ nrm2,
+                                const double* __restrict__ fn2, double snorm, double tol, int max_sweeps,
+                                const CocgScal* __restrict__ scal, int nsel, const int* __restrict__ cerr,
+                                cudaGraphConditionalHandle h) {
+  int it = 0, worst = 0;  // worst: 2 = an iteration limit, 1 = another non-zero status word
+  if (scal != nullptr)
+    for (int q = threadIdx.x; q < nsel; q += 32) {
+      it = max(it, scal[q].iters);
+      const int sq = scal[q].status;
+      worst = max(worst, sq == 4 ? 2 : (sq != 0 ? 1 : 0));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    it = max(it, __shfl_xor_sync(0xffffffffu, it, o));
+    worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  }
+  if (threadIdx.x != 0) return;
+  RefineRec r = *rec;
+  r.sweeps += 1;
+  r.max_iters = max(r.max_iters, it);
+  int st = worst == 2 ? RR_ITER_LIMIT : (worst == 1 ? RR_NUMERIC : RR_OK);
+  if (cerr != nullptr && cerr[0] != 0) st = RR_TIMEOUT;
+  const double rn = sqrt(nrm2[0]), un = sqrt(nrm2[1]), fn = sqrt(fn2[0]);
+  const double rel = rn / fn, eta = rn / (snorm * un + fn);
+  if (st == RR_OK && !(fabs(rel) <= 1.7e308)) st = RR_NUMERIC;
+  const bool more = st == RR_OK && !(eta <= tol || eta > 0.5 * r.eta_prev) && r.sweeps < max_sweeps;
+  r.rel = rel;
+  r.eta = eta;
+  r.eta_prev = eta;
+  r.status = st;
+  *rec = r;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 void launch_energy_cells(int d, int N, const double* c2, const double* y, const double* z, int64_t nall, int ntimes,
@@ -1743,9 +1792,22 @@ void launch_energy_cells(int d, int N, const double* c2, const double* y, const 
   count(2);
 }
 
-void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, cudaStream_t s) {
+void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, int* bodies,
+                          cudaStream_t s) {
   count(1);
-  k_cocg_continue<<<1, 128, 0, s>>>(scal, nmodes, handle);
+  k_cocg_continue<<<1, 128, 0, s>>>(scal, nmodes, handle, bodies);
+}
+
+void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, cudaStream_t s) {
+  count(1);
+  k_refine_init<<<1, 1, 0, s>>>(rec, fn2, h);
+}
+
+void launch_refine_decide(RefineRec* rec, const double* nrm2, const double* fn2, double snorm, double tol,
+                          int max_sweeps, const CocgScal* scal, int nsel, const int* cerr,
+                          cudaGraphConditionalHandle h, cudaStream_t s) {
+  count(1);
+  k_refine_decide<<<1, 32, 0, s>>>(rec, nrm2, fn2, snorm, tol, max_sweeps, scal, nsel, cerr, h);
 }
 
 size_t time_band_smem(int nt) { return (size_t)nt * (7 * sizeof(double) + sizeof(double) + sizeof(int)); }

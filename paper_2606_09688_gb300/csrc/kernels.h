@@ -49,8 +49,28 @@ template <typename R>
 void launch_update_p(cx<R>* p, const cx<R>* z, const CocgScal* scal, int nmodes, int64_t n, int64_t stride,
                      int first, cudaStream_t s);
 void launch_cocg_activate(CocgScal* scal, int nmodes, cudaStream_t s);
-// Sets the condition of a graph WHILE node: non-zero while any mode is active.
-void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, cudaStream_t s);
+// Sets the condition of a graph WHILE node: non-zero while any mode is active;
+// bodies (device, may be null) counts the calls.
+void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditionalHandle handle, int* bodies,
+                          cudaStream_t s);
+
+// Record of a component solve that runs entirely on the device: one CUDA
+// graph whose WHILE node runs the refinement sweeps (each with its COCG loop in
+// a nested WHILE node) and whose stopping test is taken by k_refine_decide.
+struct RefineRec {
+  double eta, rel, eta_prev;  // backward error and relative residual of the last sweep; the sweep before
+  int sweeps, status, max_iters, inner_bodies;
+};
+enum { RR_OK = 0, RR_NUMERIC = 1, RR_ITER_LIMIT = 2, RR_TIMEOUT = 3 };
+// Clears the record; the sweep loop runs when ||F||^2 (fn2[0]) is positive.
+void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, cudaStream_t s);
+// After a sweep: nrm2 = (||R||^2, ||U||^2), fn2 = ||F||^2.  Stops on
+// eta = ||R|| / (snorm ||U|| + ||F||) <= tol, when eta no longer halves, after
+// max_sweeps, on a COCG status word (scal may be null), a copy timeout
+// (cerr[0] != 0, may be null) or a non-finite residual.
+void launch_refine_decide(RefineRec* rec, const double* nrm2, const double* fn2, double snorm, double tol,
+                          int max_sweeps, const CocgScal* scal, int nsel, const int* cerr,
+                          cudaGraphConditionalHandle h, cudaStream_t s);
 
 // Time transforms of the eigenbasis method (FP64 matrices):
 // G[q][a] = sum_i W[q][i] R[i][a];  U[i][a] += sum_q w_q Re(V[i][q] X[q][a]).

@@ -248,13 +248,16 @@ struct Component {
   // iterations, captured at setup on the component stream.
   cudaGraphExec_t g_init = nullptr, g_iter = nullptr;
   int64_t g_init_nodes = 0, g_iter_nodes = 0;
-  // the whole inner loop on the device: a WHILE node whose body is
-  // kIterPerGraph iterations and the test "any mode still active"
-  cudaGraphExec_t g_while = nullptr;
-  int64_t g_while_nodes = 0;       // kernels per body execution
-  int g_while_body = 0;            // COCG iterations per body
-  bool inner_pending = false;      // a device-side loop ran; its status is read after the next sync
   double fnorm = -1.0;             // ||F|| of the forward right-hand side (constant after setup)
+  // The whole forward solve as one graph (st_options.device_loop > 0): the
+  // refinement sweeps in a WHILE node, the COCG loop of a sweep in a nested
+  // one; the host reads its record once the call's work is done.
+  cudaGraphExec_t g_solve = nullptr;
+  int64_t gs_pro_nodes = 0, gs_sweep_nodes = 0, gs_inner_nodes = 0;  // kernels: prologue, sweep, inner body
+  RefineRec* rec = nullptr;    // device
+  RefineRec* rec_h = nullptr;  // pinned copy
+  double* fn2 = nullptr;       // ||F||^2 (device)
+  bool rec_pending = false;    // a graph solve was enqueued; its record is not read yet
 };
 
 // Algorithmic flops per node of the complex Q1 stencil (K and M parts with
@@ -280,6 +283,7 @@ struct st_handle {
   int* dev_err = nullptr;
   int* solve_err = nullptr;  // set by bounded waits inside the band solve
   cudaEvent_t entry_ev = nullptr;
+  cudaStream_t join = nullptr;  // waits for the components of a call whose solves run as graphs
   // Back-to-back st_solve_combine calls overlap (st_solve_combine): api_seq
   // counts the calls that may enqueue work on the handle's stream, sc_seq is
   // the count at the last st_solve_combine, sc_parity the pair buffer its
@@ -350,12 +354,14 @@ struct st_handle {
     for (auto& c : comps) {
       if (c->g_init) cudaGraphExecDestroy(c->g_init);
       if (c->g_iter) cudaGraphExecDestroy(c->g_iter);
-      if (c->g_while) cudaGraphExecDestroy(c->g_while);
+      if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
       if (c->cscalar_h) cudaFreeHost(c->cscalar_h);
+      if (c->rec_h) cudaFreeHost(c->rec_h);
       if (c->cs) cudaStreamDestroy(c->cs);
       if (c->done) cudaEventDestroy(c->done);
     }
     if (entry_ev) cudaEventDestroy(entry_ev);
+    if (join) cudaStreamDestroy(join);
     for (auto e : sc_done_ev)
       if (e) cudaEventDestroy(e);
     for (auto& r : prof) {
@@ -1253,65 +1259,7 @@ template <typename R> st_status capture_graphs(st_handle* h, Component& c) {
       c.g_iter_nodes = nodes;
     }
   }
-  // the device-side loop: WHILE (any mode active) { k iterations; update the condition }
-  if (h->opt.device_loop > 0) {
-    cudaGraph_t wg = nullptr;
-    ST_CUDA(h, cudaGraphCreate(&wg, 0));
-    cudaGraphConditionalHandle hnd;
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cudaGraphNode_t node;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&hnd, wg, 1, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) {
-      cp.conditional.handle = hnd;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      e = cudaGraphAddNode(&node, wg, nullptr, nullptr, 0, &cp);
-    }
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(wg);
-      return fail(h, ST_ERR_CUDA, std::string("conditional graph node: ") + cudaGetErrorString(e));
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    const int64_t l0 = kernel_launch_count();
-    ST_CUDA(h, cudaStreamBeginCaptureToGraph(c.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < h->opt.device_loop; ++k) cocg_iteration<R>(h, c);
-    launch_cocg_continue(c.scal, c.nsel, hnd, c.cs);
-    cudaGraph_t captured = nullptr;
-    ST_CUDA(h, cudaStreamEndCapture(c.cs, &captured));
-    cudaGraphExec_t ge = nullptr;
-    e = cudaGraphInstantiate(&ge, wg, 0);
-    cudaGraphDestroy(wg);
-    if (e != cudaSuccess) return fail(h, ST_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
-    c.g_while = ge;
-    c.g_while_nodes = kernel_launch_count() - l0;
-    c.g_while_body = h->opt.device_loop;
-  }
   return check_launch(h, "graph capture");
-}
-
-// Status of a device-side inner loop (st_solve_component's COCG run as one
-// graph launch): read after the stream has been synchronised by the caller.
-st_status check_inner(Component& c, int& iters_out) {
-  iters_out = 0;
-  if (!c.inner_pending) return ST_OK;
-  c.inner_pending = false;
-  ST_CUDAC(c, cudaMemcpy(c.scal_h.data(), c.scal, c.nsel * sizeof(CocgScal), cudaMemcpyDeviceToHost));
-  c.d2h += (int64_t)(c.nsel * sizeof(CocgScal));
-  int worst = 0;
-  for (const auto& q : c.scal_h) {
-    iters_out = std::max(iters_out, q.iters);
-    if (q.status != 0) worst = q.status;
-  }
-  // the loop body ran once per `device_loop` iterations of the slowest mode
-  // (one body was counted at launch)
-  if (c.g_while_body > 0) {
-    const int bodies = std::max(1, (iters_out + c.g_while_body - 1) / c.g_while_body);
-    note_launches((int)(c.g_while_nodes * (bodies - 1)));
-  }
-  if (worst == 4) return cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
-  if (worst != 0) return cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
-  return ST_OK;
 }
 
 // Solve (lam_q M + K) x_q = g_q for every mode; w.G holds g, the result lands in w.X.
@@ -1329,15 +1277,6 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
     return ccheck(c, "direct band solve");
   }
   const int max_iter = h->opt.max_iter > 0 ? h->opt.max_iter : 1000;
-  if (!h->prof_on && c.g_init != nullptr && c.g_while != nullptr) {
-    // the whole loop on the device: no host round trip; the modes' status
-    // words are read after the sweep's norms (check_inner)
-    ST_CUDAC(c, cudaGraphLaunch(c.g_init, s));
-    ST_CUDAC(c, cudaGraphLaunch(c.g_while, s));
-    note_launches((int)(c.g_init_nodes + c.g_while_nodes));
-    c.inner_pending = true;
-    return ST_OK;
-  }
   const bool graphs = !h->prof_on && c.g_init != nullptr && c.g_iter != nullptr;
   if (graphs) {
     ST_CUDAC(c, cudaGraphLaunch(c.g_init, s));
@@ -1366,12 +1305,6 @@ template <typename R> st_status inner_solve(st_handle* h, Component& c, int& ite
   for (const auto& q : c.scal_h) {
     iters_out = std::max(iters_out, q.iters);
     if (q.status != 0) worst = q.status;
-  }
-  // the loop body ran once per `device_loop` iterations of the slowest mode
-  // (one body was counted at launch)
-  if (c.g_while_body > 0) {
-    const int bodies = std::max(1, (iters_out + c.g_while_body - 1) / c.g_while_body);
-    note_launches((int)(c.g_while_nodes * (bodies - 1)));
   }
   if (worst == 4) return cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
   if (worst != 0) return cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
@@ -1463,7 +1396,11 @@ st_status sweep_space_eig(st_handle* h, Component& c, const SolveIO& io, const d
   return ccheck(c, "space eigenbasis sweep");
 }
 
+st_status enqueue_graph_solve(st_handle* h, Component& c);
+bool graph_solves(const st_handle* h);
+
 st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint) {
+  if (!adjoint && graph_solves(h) && c.g_solve != nullptr) return enqueue_graph_solve(h, c);
   st_status s = ST_OK;
   if (!adjoint && (s = assemble_rhs(h, c)) != ST_OK) return s;
   const size_t n = (size_t)c.nx * c.nt;
@@ -1509,13 +1446,7 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
                          c.cs));
     double rn = 0.0, un = 0.0;
     if ((s = read_norm2(h, c, c.Rv, io.sol, (int64_t)n, rn, un)) != ST_OK) return s;
-    // the inner loop of this sweep ran on the device: its status words now
-    int dev_iters = 0;
-    if ((s = check_inner(c, dev_iters)) != ST_OK) {
-      c.info.status = s;
-      return s;
-    }
-    c.info.max_inner_iters = std::max(c.info.max_inner_iters, std::max(iters, dev_iters));
+    c.info.max_inner_iters = std::max(c.info.max_inner_iters, iters);
     rel = rn / fn;
     eta = rn / (c.Snorm * un + fn);
     if (!std::isfinite(rel)) {
@@ -1535,6 +1466,194 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
   }
   return ST_OK;
 }
+
+// ------------------------------------------------- solves as one graph
+// Adds a WHILE node with condition handle hnd after the work captured so far
+// on stream s and returns its (empty) body graph.
+cudaError_t capture_add_while(cudaStream_t s, cudaGraphConditionalHandle hnd, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cst != cudaStreamCaptureStatusActive || g == nullptr) return cudaErrorIllegalState;
+  const std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, dv.empty() ? nullptr : dv.data(), nullptr, dv.size(), &cp);
+  if (e != cudaSuccess) return e;
+  *body = cp.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Every kernel node of g at stream priority prio (kernels in conditional
+// bodies are launched by the device, not through the component's stream).
+cudaError_t set_kernel_priority(cudaGraph_t g, int prio) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if ((e = cudaGraphGetNodes(g, nodes.data(), &n)) != cudaSuccess) return e;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nd, &t)) != cudaSuccess) return e;
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeAttrValue v{};
+    v.priority = prio;
+    if ((e = cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The forward solve of a component as one CUDA graph, captured on its stream:
+//   U = 0, R = F, ||F||^2, condition (k_refine_init);
+//   WHILE (condition) {                       -- one refinement sweep
+//     time eigenbasis: G = W R; COCG start; WHILE (any mode active)
+//       { device_loop COCG iterations; condition }; U += Re(V X)
+//     (direct components: the banded solve; space eigenbasis: its sweep)
+//     R = F - S U; ||R||^2, ||U||^2; stopping test (k_refine_decide) }
+// The same kernels as the host-driven loop, in the same order; the host reads
+// the record (sweeps, backward error, status) once per call.
+template <typename R> st_status capture_solve_graph(st_handle* h, Component& c) {
+  const SolveIO io = forward_io(c);
+  const int64_t n = c.nx * (int64_t)c.nt;
+  const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-14;
+  const int max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 8;
+  const bool iterative = c.method == 0 && !c.direct;
+  if (c.method == 1 && time_band_smem(c.nt) > kTimeBandMaxSmem)
+    return fail(h, ST_ERR_ARG, "device solve: time band solve of this size not supported");
+  c.rec = h->alloc<RefineRec>(1);
+  c.fn2 = h->alloc<double>(1);
+  ST_NEED(h, c.rec);
+  ST_NEED(h, c.fn2);
+  ST_CUDA(h, cudaMallocHost(&c.rec_h, sizeof(RefineRec)));
+  int prio_lo = 0, prio_hi = 0;
+  ST_CUDA(h, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  cudaGraph_t g = nullptr, sweep = nullptr, inner = nullptr;
+  ST_CUDA(h, cudaGraphCreate(&g, 0));
+  std::string where;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r, const char* what) {
+    if (r != cudaSuccess && e == cudaSuccess) {
+      e = r;
+      where = what;
+    }
+    return e == cudaSuccess;
+  };
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraphConditionalHandle hs{}, hi{};
+  // prologue
+  int64_t l0 = kernel_launch_count();
+  if (ok(cudaGraphConditionalHandleCreate(&hs, g, 0, cudaGraphCondAssignDefault), "sweep condition") &&
+      ok(cudaStreamBeginCaptureToGraph(c.cs, g, nullptr, nullptr, 0, mode), "prologue capture")) {
+    cudaMemsetAsync(io.sol, 0, (size_t)n * sizeof(double), c.cs);
+    cudaMemcpyAsync(c.Rv, io.rhs, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c.cs);
+    launch_norm2(io.rhs, n, c.cpart, c.fn2, c.cs);
+    launch_refine_init(c.rec, c.fn2, hs, c.cs);
+    ok(capture_add_while(c.cs, hs, &sweep), "sweep node");
+    cudaGraph_t out = nullptr;
+    ok(cudaStreamEndCapture(c.cs, &out), "prologue capture end");
+  }
+  c.gs_pro_nodes = kernel_launch_count() - l0;
+  // one sweep
+  l0 = kernel_launch_count();
+  if (e == cudaSuccess && ok(cudaStreamBeginCaptureToGraph(c.cs, sweep, nullptr, nullptr, 0, mode), "sweep capture")) {
+    if (c.method == 1) {
+      launch_gemm_right(c.Rv, c.Phi, c.KU, c.nt, c.nx, 0, 0, c.cs);
+      launch_time_band_solve(io.lu_ab, io.lu_piv, c.KU, c.nt, c.nx, c.kl, c.ku, c.cs);
+      launch_gemm_right(c.KU, c.PhiT, io.sol, c.nt, c.nx, 1, 1, c.cs);
+    } else {
+      Work<R>& w = work_of<R>(c);
+      launch_fwd_transform<R>(io.Wf, c.Rv, w.G, c.nsel, c.nt, c.nx, c.cs);
+      if (c.direct) {
+        band_solve<R>(c, w.G, w.X, nullptr, c.nx, c.cs);
+      } else {
+        c.nactive = c.nsel;
+        cocg_start<R>(h, c);
+        if (ok(cudaGraphConditionalHandleCreate(&hi, sweep, 0, cudaGraphCondAssignDefault), "inner condition")) {
+          launch_cocg_continue(c.scal, c.nsel, hi, nullptr, c.cs);
+          ok(capture_add_while(c.cs, hi, &inner), "inner node");
+        }
+      }
+      launch_back_transform<R>(io.Vb, c.td->wq, w.X, io.sol, c.nsel, c.nt, c.nx, c.cs);
+    }
+    launch_residual(c.sl->geo, c.sl->sc, c.sl->c2d, io.sol, io.rhs, io.Ab, io.Bb, c.KU, c.MU, c.Rv, c.nt, c.cs);
+    launch_norm2(c.Rv, n, c.cpart, c.cscalar, c.cs);
+    launch_norm2(io.sol, n, c.cpart, c.cscalar + 1, c.cs);
+    launch_refine_decide(c.rec, c.cscalar, c.fn2, c.Snorm, tol, max_sweeps, iterative ? c.scal : nullptr, c.nsel,
+                         c.cerr, hs, c.cs);
+    cudaGraph_t out = nullptr;
+    ok(cudaStreamEndCapture(c.cs, &out), "sweep capture end");
+  }
+  c.gs_sweep_nodes = kernel_launch_count() - l0;
+  // the COCG loop body
+  l0 = kernel_launch_count();
+  if (e == cudaSuccess && iterative &&
+      ok(cudaStreamBeginCaptureToGraph(c.cs, inner, nullptr, nullptr, 0, mode), "inner capture")) {
+    for (int k = 0; k < h->opt.device_loop; ++k) cocg_iteration<R>(h, c);
+    launch_cocg_continue(c.scal, c.nsel, hi, &c.rec->inner_bodies, c.cs);
+    cudaGraph_t out = nullptr;
+    ok(cudaStreamEndCapture(c.cs, &out), "inner capture end");
+  }
+  c.gs_inner_nodes = iterative ? kernel_launch_count() - l0 : 0;
+  if (e == cudaSuccess) ok(cudaGetLastError(), "captured launches");
+  if (e == cudaSuccess) ok(set_kernel_priority(g, prio_hi), "priority");
+  if (e == cudaSuccess) ok(set_kernel_priority(sweep, prio_hi), "priority");
+  if (e == cudaSuccess && inner != nullptr) ok(set_kernel_priority(inner, prio_hi), "priority");
+  cudaGraphExec_t ge = nullptr;
+  if (e == cudaSuccess) ok(cudaGraphInstantiate(&ge, g, 0), "instantiation");
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, ST_ERR_CUDA, "solve graph (" + where + "): " + cudaGetErrorString(e));
+  }
+  c.g_solve = ge;
+  return ST_OK;
+}
+
+// Enqueues a component's forward solve as its graph, then the copy of its record.
+st_status enqueue_graph_solve(st_handle* h, Component& c) {
+  st_status s = assemble_rhs(h, c);
+  if (s != ST_OK) return s;
+  c.info = st_solve_info{};
+  c.info.status = ST_OK;
+  ST_CUDAC(c, cudaGraphLaunch(c.g_solve, c.cs));
+  ST_CUDAC(c, cudaMemcpyAsync(c.rec_h, c.rec, sizeof(RefineRec), cudaMemcpyDeviceToHost, c.cs));
+  c.d2h += (int64_t)sizeof(RefineRec);
+  note_launches((int)c.gs_pro_nodes);
+  c.rec_pending = true;
+  return ccheck(c, "solve graph");
+}
+
+// Status of a graph solve, once the host has synchronised with an event that
+// follows the record's copy: the same outcomes as the host-driven loop.
+st_status finish_graph_solve(st_handle* h, Component& c) {
+  if (!c.rec_pending) return ST_OK;
+  c.rec_pending = false;
+  const RefineRec r = *c.rec_h;
+  note_launches((int)(r.sweeps * c.gs_sweep_nodes + r.inner_bodies * c.gs_inner_nodes));
+  c.info.sweeps = r.sweeps;
+  c.info.max_inner_iters = r.max_iters;
+  c.info.rel_residual = r.rel;
+  c.info.backward_error = r.eta;
+  const double tol = h->opt.tol > 0 ? h->opt.tol : 1e-14;
+  st_status st = ST_OK;
+  if (r.status == RR_TIMEOUT) st = cfail(c, ST_ERR_TIMEOUT, "a bounded copy wait in the banded solve timed out");
+  else if (r.status == RR_ITER_LIMIT) st = cfail(c, ST_ERR_NOT_CONVERGED, "COCG reached its iteration limit");
+  else if (r.status != RR_OK) st = cfail(c, ST_ERR_NUMERIC, "COCG breakdown or non-finite value");
+  c.solved = r.status == RR_OK;
+  if (st == ST_OK && r.sweeps > 0 && r.eta > 1e3 * tol && r.eta > 1e-12)
+    st = cfail(c, ST_ERR_NOT_CONVERGED, "refinement did not reach the backward-error target");
+  c.info.status = st;
+  return st;
+}
+
+bool graph_solves(const st_handle* h) { return h->opt.device_loop > 0 && !h->prof_on; }
 
 // Execution context of a component: stream, completion event, reduction
 // scratch, and its workspace prepared for the handle's precision.
@@ -1565,6 +1684,24 @@ st_status setup_context(st_handle* h, Component& c) {
       s = c.inner64 ? capture_graphs<double>(h, c) : capture_graphs<float>(h, c);
       if (s != ST_OK) return s;
     }
+  }
+  if (h->opt.device_loop > 0)
+    return (c.method == 0 && !c.inner64) ? capture_solve_graph<float>(h, c) : capture_solve_graph<double>(h, c);
+  return ST_OK;
+}
+
+// Waits (one host synchronisation) until every listed component's stream has
+// passed its completion event, then reads the records of their graph solves.
+st_status join_graph_solves(st_handle* h, const std::vector<Component*>& cs, std::vector<st_status>& st) {
+  if (h->join == nullptr) ST_CUDA(h, cudaStreamCreateWithFlags(&h->join, cudaStreamNonBlocking));
+  for (Component* c : cs) {
+    ST_CUDA(h, cudaEventRecord(c->done, c->cs));
+    ST_CUDA(h, cudaStreamWaitEvent(h->join, c->done, 0));
+  }
+  ST_CUDA(h, cudaStreamSynchronize(h->join));
+  for (size_t i = 0; i < cs.size(); ++i) {
+    const st_status r = finish_graph_solve(h, *cs[i]);
+    if (st[i] == ST_OK) st[i] = r;
   }
   return ST_OK;
 }
@@ -1841,13 +1978,21 @@ st_status run_solves(st_handle* h, int k0, int k1, bool adjoint, st_solve_info* 
     Component& c = *h->comps[i];
     st[i - k0] = solve_one(h, c, adjoint ? adjoint_io(c) : forward_io(c), adjoint);
   };
-  if (k1 - k0 > 1 && !h->prof_on) {
+  // graph solves: every component enqueued from this thread, one wait for all
+  const bool graphs = !adjoint && graph_solves(h);
+  if (k1 - k0 > 1 && !h->prof_on && !graphs) {
     std::vector<std::thread> pool;
     pool.reserve(k1 - k0);
     for (int i = k0; i < k1; ++i) pool.emplace_back(run, i);
     for (auto& t : pool) t.join();
   } else {
     for (int i = k0; i < k1; ++i) run(i);
+  }
+  if (graphs) {
+    std::vector<Component*> cs;
+    for (int i = k0; i < k1; ++i) cs.push_back(h->comps[i].get());
+    st_status js = join_graph_solves(h, cs, st);
+    if (js != ST_OK) return js;
   }
   st_status worst = ST_OK;
   st_solve_info agg{};
@@ -2164,15 +2309,28 @@ st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_
   }
   std::stable_sort(tasks.begin(), tasks.end(), [](const Task& a, const Task& b) { return a.cost > b.cost; });
   std::vector<st_status> st(tasks.size(), ST_OK);
-  std::atomic<size_t> next{0};
-  auto worker = [&]() {
-    for (size_t t = next.fetch_add(1); t < tasks.size(); t = next.fetch_add(1)) {
+  bool graphs = true;
+  for (int i = 0; i < n; ++i) graphs = graphs && graph_solves(hs[i]);
+  if (graphs) {
+    // every component's solve is one graph: all enqueued from this thread,
+    // largest first, then one host synchronisation for the whole batch
+    std::vector<Component*> cs;
+    for (size_t t = 0; t < tasks.size(); ++t) {
       Component& c = *tasks[t].h->comps[tasks[t].k];
       st[t] = solve_one(tasks[t].h, c, forward_io(c), false);
+      cs.push_back(&c);
     }
-  };
-  const int nth = (int)std::min<size_t>(tasks.size(), max_threads > 0 ? (size_t)max_threads : (size_t)32);
-  {
+    st_status js = join_graph_solves(hs[0], cs, st);
+    if (js != ST_OK) return js;
+  } else {
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t t = next.fetch_add(1); t < tasks.size(); t = next.fetch_add(1)) {
+        Component& c = *tasks[t].h->comps[tasks[t].k];
+        st[t] = solve_one(tasks[t].h, c, forward_io(c), false);
+      }
+    };
+    const int nth = (int)std::min<size_t>(tasks.size(), max_threads > 0 ? (size_t)max_threads : (size_t)32);
     std::vector<std::thread> pool;
     for (int i = 0; i < nth; ++i) pool.emplace_back(worker);
     for (auto& th : pool) th.join();
@@ -2295,8 +2453,19 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     }
     cv.notify_all();
   };
+  // graph solves are enqueued inline (they return at once); host-driven
+  // solves run on a thread each, except when profiling
+  const bool graphs = graph_solves(h);
   std::vector<std::thread> pool;
-  if (!h->prof_on) {
+  if (graphs) {
+    // largest first: the finest components are the step's critical path
+    std::vector<int> byc(nc);
+    for (int i = 0; i < nc; ++i) byc[i] = i;
+    std::stable_sort(byc.begin(), byc.end(), [&](int a, int b) {
+      return h->comps[a]->nx * h->comps[a]->nt > h->comps[b]->nx * h->comps[b]->nt;
+    });
+    for (int i : byc) run(i);
+  } else if (!h->prof_on) {
     pool.reserve(nc);
     for (int i = 0; i < nc; ++i) pool.emplace_back(run, i);
   }
@@ -2305,7 +2474,9 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     const int c0 = t->first[lev], c1 = t->first[lev + 1];
     for (int o = c0; o < c1 && !failed; ++o) {
       const int k = t->order[o];
-      if (h->prof_on) {
+      if (graphs) {
+        // enqueued above
+      } else if (h->prof_on) {
         run(k);
       } else {
         std::unique_lock<std::mutex> lock(mu);
@@ -2322,6 +2493,21 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
     if (le != nullptr) cudaEventRecord(le, h->stream);
   }
   for (auto& th : pool) th.join();
+  if (graphs) {
+    // one host synchronisation: the solves' records (the levels may still run)
+    std::vector<Component*> cs;
+    std::vector<st_status> gst;
+    std::vector<int> idx;
+    for (int i = 0; i < nc; ++i)
+      if (done[i] && h->comps[i]->rec_pending) {
+        cs.push_back(h->comps[i].get());
+        gst.push_back(st[i]);
+        idx.push_back(i);
+      }
+    st_status js = join_graph_solves(h, cs, gst);
+    if (js != ST_OK) return js;
+    for (size_t j = 0; j < idx.size(); ++j) st[idx[j]] = gst[j];
+  }
   st_status worst = ST_OK;
   st_solve_info agg{};
   for (int i = 0; i < nc; ++i) {

@@ -38,8 +38,8 @@ def _component(s, jx, jt):
 def test_inner_iteration_limit_reports_not_converged(device_loop):
     from paper_2606_09688_gb300 import Solver, StError
     from paper_2606_09688_gb300 import st as B
-    # grids above 500 unknowns go through multigrid-preconditioned COCG; with the
-    # device-side loop the modes' status words are read after the sweep
+    # grids above 500 unknowns go through multigrid-preconditioned COCG; with graph
+    # solves the modes' status words are read by the device-side stopping test
     with Solver(W.layered_2d(8, 2), max_direct_rows=500, max_iter=1, device_loop=device_loop) as s:
         with pytest.raises(StError) as e:
             s.solve(_component(s, 6, 2))
@@ -47,10 +47,13 @@ def test_inner_iteration_limit_reports_not_converged(device_loop):
         assert "iteration limit" in str(e.value)
 
 
-def test_refinement_sweep_limit_reports_not_converged():
+@pytest.mark.parametrize("device_loop", [0, 4])
+def test_refinement_sweep_limit_reports_not_converged(device_loop):
     from paper_2606_09688_gb300 import ST_FP32_IR, Solver, StError
     from paper_2606_09688_gb300 import st as B
-    with Solver(W.layered_2d(8, 2), precision=ST_FP32_IR, max_sweeps=1, tol=1e-15) as s:
+    # with graph solves the sweep limit is applied by the device-side stopping test
+    with Solver(W.layered_2d(8, 2), precision=ST_FP32_IR, max_sweeps=1, tol=1e-15,
+                device_loop=device_loop) as s:
         with pytest.raises(StError) as e:
             s.solve(_component(s, 6, 2))
         assert e.value.code == B.ST_ERR_NOT_CONVERGED
@@ -67,11 +70,13 @@ def test_allocation_cap_reports_oom_and_a_sufficient_cap_solves():
         assert s.solve(-1).status == 0
 
 
-def test_bounded_copy_wait_runs_out_and_context_stays_usable():
+@pytest.mark.parametrize("device_loop", [0, 4])
+def test_bounded_copy_wait_runs_out_and_context_stays_usable(device_loop):
     from paper_2606_09688_gb300 import Solver, StError
     from paper_2606_09688_gb300 import st as B
     p = W.standing_wave(3, 6, 2)          # (4,2): 15^3 grid, half bandwidth 241, solved directly
-    with Solver(p, wait_cycles=200000, inject_stall=1) as s:
+    # with graph solves the timeout flag is read by the device-side stopping test
+    with Solver(p, wait_cycles=200000, inject_stall=1, device_loop=device_loop) as s:
         k = _component(s, 4, 2)
         with pytest.raises(StError) as e:
             s.solve(k)
