@@ -67,6 +67,10 @@ struct Geo {
 template <typename R> struct StencilCoefT {
   R ke[27];
   R mtot[27];
+  // damped inverse diagonal omega / (K + lam_q M)_aa per mode and node of a
+  // multigrid level (mode-major, the level's vector stride), used by the FP64
+  // Jacobi sweeps when set; null = formed on the fly
+  const cx<R>* dinv = nullptr;
 };
 using StencilCoef = StencilCoefT<double>;
 inline StencilCoefT<float> to_float(const StencilCoef& s) {

@@ -93,8 +93,19 @@ template <int D> __device__ __forceinline__ bool neighbour(const int i[3], int s
 }
 
 // ------------------------------------------------------------------ stencils
-__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+// Reciprocal for the damping of a Jacobi sweep: the fast approximate FP32
+// division (2 ulp) in FP32 sweeps, whose smoothing only feeds FP64
+// refinement; the correctly rounded one in FP64.
+__device__ __forceinline__ float rcp_rn(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
+
+// The value of the lane below / above (lane 0 and lane 31 get their own).
+template <typename R> __device__ __forceinline__ cx<R> shfl_up1(cx<R> v) {
+  return mk<R>(__shfl_up_sync(0xffffffffu, v.re, 1), __shfl_up_sync(0xffffffffu, v.im, 1));
+}
+template <typename R> __device__ __forceinline__ cx<R> shfl_down1(cx<R> v) {
+  return mk<R>(__shfl_down_sync(0xffffffffu, v.re, 1), __shfl_down_sync(0xffffffffu, v.im, 1));
+}
 
 // s * a / b with one reciprocal of |b|^2 (two divisions in the textbook form).
 template <typename R> __device__ __forceinline__ cx<R> scaled_div(R s, cx<R> a, cx<R> b) {
@@ -141,7 +152,7 @@ __global__ void __launch_bounds__(512) k_stencil(Geo g, StencilCoefT<R> sc, cons
     const cx<R> diag = fma_s(sc.mtot[CEN], l, mk<R>(kr[CEN], R(0)));
     const int64_t base = (int64_t)q * stride + a;
     if (OP == OP_JACOBI_ZERO) {
-      y[base] = scaled_div(omega, b[base], diag);
+      y[base] = (sizeof(R) == 8 && sc.dinv != nullptr) ? sc.dinv[base] * b[base] : scaled_div(omega, b[base], diag);
       continue;
     }
     cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
@@ -160,9 +171,27 @@ __global__ void __launch_bounds__(512) k_stencil(Geo g, StencilCoefT<R> sc, cons
       y[base] = b[base] - Ax;
     } else {  // OP_JACOBI
       const cx<R> xo = x[base];
-      y[base] = xo + scaled_div(omega, b[base] - Ax, diag);
+      const cx<R> r = b[base] - Ax;
+      y[base] = (sizeof(R) == 8 && sc.dinv != nullptr) ? fma_c(sc.dinv[base], r, xo) : xo + scaled_div(omega, r, diag);
     }
   }
+}
+
+// Damped inverse diagonal omega / (K(c2) + lam_q M)_aa of a level for every
+// mode (set-up; the same diagonal as the sweeps form on the fly).
+template <int D, typename R>
+__global__ void k_jacobi_dinv(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2, const cx<R>* __restrict__ lam,
+                              R omega, int64_t stride, cx<R>* __restrict__ dinv) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  constexpr int NS = ipow3(D), CEN = (NS - 1) / 2;
+  int i[3] = {0, 0, 0};
+  decode<D>(a, g, i);
+  R kr[NS];
+  cell_sums<D, R>(c2, g.N, i, kr);
+  const int q = blockIdx.y;
+  const cx<R> diag = fma_s(sc.mtot[CEN], lam[q], mk<R>(kr[CEN] * sc.ke[CEN], R(0)));
+  dinv[(int64_t)q * stride + a] = cdiv(mk<R>(omega, R(0)), diag);
 }
 
 // 2D variant with the operand staged in shared memory: a CTA takes a
@@ -238,7 +267,9 @@ __global__ void __launch_bounds__(256) k_stencil_tile2(Geo g, StencilCoefT<R> sc
       } else if (OP == OP_RESID) {
         y[base] = b[base] - Ax;
       } else {  // OP_JACOBI
-        y[base] = xs[m][r + 1][tx + 1] + scaled_div(omega, b[base] - Ax, diag);
+        const cx<R> res = b[base] - Ax;
+        y[base] = (sizeof(R) == 8 && sc.dinv != nullptr) ? fma_c(sc.dinv[base], res, xs[m][r + 1][tx + 1])
+                                     : xs[m][r + 1][tx + 1] + scaled_div(omega, res, diag);
       }
     }
   }
@@ -246,25 +277,22 @@ __global__ void __launch_bounds__(256) k_stencil_tile2(Geo g, StencilCoefT<R> sc
 
 // 2D variant streaming down columns: a warp owns 30 consecutive columns of
 // interior nodes (its lanes 0 and 31 hold the halo columns) and walks a strip
-// of `rows` rows (32 on large grids, fewer on small ones, so that small grids
-// still spread over many warps).  The x values of rows i-1, i, i+1 and the c^2 cells of
-// cell rows i, i+1 roll in registers; the left and right neighbours of a new
-// row come from the adjacent lanes through a small shared-memory row per warp
-// (double-buffered).  Per node and mode the kernel reads x and b once and
-// writes y once (three global requests instead of nine).  The loads of x, b
-// and c^2 run PF rows ahead of the row being computed, so that a warp keeps
-// PF rows of requests in flight instead of waiting one load latency per row.
+// of `rows` rows (as many strips as fill the device once).  The x values of
+// rows i-1, i, i+1 and the c^2 cells of cell rows i, i+1 roll in registers;
+// the left and right neighbours of a new row come from the adjacent lanes by
+// warp shuffles.  Per node and mode the kernel reads x and b once and writes y
+// once (three global requests instead of nine).  The loads of x, b and c^2 run
+// PF rows ahead of the row being computed, so that a warp keeps PF rows of
+// requests in flight instead of waiting one load latency per row.
 constexpr int kColWarps = 4, kColOut = 30;
 template <typename R, int OP, int MQ>
-__global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
+__global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 : 1) k_stencil_col2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
                                                                   const cx<R>* __restrict__ x,
                                                                   const cx<R>* __restrict__ b, cx<R>* __restrict__ y,
                                                                   const cx<R>* __restrict__ lam,
                                                                   const CocgScal* __restrict__ scal, int nmodes,
                                                                   int64_t stride, R omega, int rows) {
-  constexpr int PF = MQ >= 4 ? 1 : (MQ == 2 ? 2 : 4);  // rows of loads in flight ahead of the computed row
-  __shared__ cx<R> srow[kColWarps][2][MQ][32];
-  __shared__ R scell[kColWarps][2][32];
+  constexpr int PF = MQ >= 4 ? 1 : (MQ == 2 ? 2 : 3);  // rows of loads in flight ahead of the computed row
   const int n = g.n, N = g.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ix = (blockIdx.x * kColWarps + warp) * kColOut - 1 + lane;
@@ -273,7 +301,6 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilC
   const bool colok = ix >= 0 && ix < n;
   const bool cellok = ix >= 0 && ix < N;
   const bool writer = lane >= 1 && lane <= kColOut && colok;
-  const int lm1 = lane > 0 ? lane - 1 : 0, lp1 = lane < 31 ? lane + 1 : 31;
   const cx<R> zero = mk<R>(0, 0);
   bool act[MQ];
   const cx<R>* xq[MQ];
@@ -311,30 +338,25 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilC
     }
     cf[f] = ldc(r0 + 2 + f);
   }
-  // neighbours (left, right) of rows r0-1 and r0 through the row buffers
-  cx<R> la[MQ], ra[MQ], lb[MQ], rb[MQ], lc[MQ], rc[MQ];
+  // neighbours (left, right) of rows r0-1 and r0 from the adjacent lanes;
+  // h = left + 4 centre + right of a row: the mass stencil is
+  // m0 (1, 4, 1) (x) (1, 4, 1), so M x = m0 (h(i-1) + h(i+1)) + 4 m0 h(i)
+  cx<R> la[MQ], ra[MQ], lb[MQ], rb[MQ], lc[MQ], rc[MQ], ha[MQ], hb[MQ];
+  const R m0 = sc.mtot[0], m3 = sc.mtot[3];
   R car, cbr;  // cells of column ix + 1
   {
 #pragma unroll
     for (int m = 0; m < MQ; ++m) {
-      srow[warp][0][m][lane] = xa[m];
-      srow[warp][1][m][lane] = xb[m];
+      la[m] = shfl_up1(xa[m]);
+      ra[m] = shfl_down1(xa[m]);
+      lb[m] = shfl_up1(xb[m]);
+      rb[m] = shfl_down1(xb[m]);
+      ha[m] = fma_s(R(4), xa[m], la[m] + ra[m]);
+      hb[m] = fma_s(R(4), xb[m], lb[m] + rb[m]);
     }
-    scell[warp][0][lane] = ca;
-    scell[warp][1][lane] = cb;
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < MQ; ++m) {
-      la[m] = srow[warp][0][m][lm1];
-      ra[m] = srow[warp][0][m][lp1];
-      lb[m] = srow[warp][1][m][lm1];
-      rb[m] = srow[warp][1][m][lp1];
-    }
-    car = scell[warp][0][lp1];
-    cbr = scell[warp][1][lp1];
-    __syncwarp();
+    car = __shfl_down_sync(0xffffffffu, ca, 1);
+    cbr = __shfl_down_sync(0xffffffffu, cb, 1);
   }
-  int buf = 0;
   const int rend = min(r0 + rows, n);
   // rows in groups of PF: queue slot f is refilled right after it is used,
   // with no register moves of loads still in flight
@@ -343,17 +365,16 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilC
     for (int f = 0; f < PF; ++f) {
       const int row = row0 + f;
       if (row >= rend) break;
-      // neighbours of row + 1 and of its cells' next row (slot f: rows row + 2)
-#pragma unroll
-      for (int m = 0; m < MQ; ++m) srow[warp][buf][m][lane] = xc[m];
-      scell[warp][buf][lane] = cf[f];
-      __syncwarp();
+      // neighbours of row + 1 and the right cell of its cell row
 #pragma unroll
       for (int m = 0; m < MQ; ++m) {
-        lc[m] = srow[warp][buf][m][lm1];
-        rc[m] = srow[warp][buf][m][lp1];
+        lc[m] = shfl_up1(xc[m]);
+        rc[m] = shfl_down1(xc[m]);
       }
-      const R cnr = scell[warp][buf][lp1];
+      const R cnr = __shfl_down_sync(0xffffffffu, cf[f], 1);
+      cx<R> hc[MQ];
+#pragma unroll
+      for (int m = 0; m < MQ; ++m) hc[m] = fma_s(R(4), xc[m], lc[m] + rc[m]);
       if (writer) {
         // cells of the node (ix, row): (ix, row), (ix+1, row), (ix, row+1), (ix+1, row+1)
         const R c00 = ca, c10 = car, c01 = cb, c11 = cbr;
@@ -377,26 +398,33 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilC
           const cx<R> l = lam[q];
           const int64_t base = (int64_t)q * stride + a;
           const cx<R> v[9] = {la[m], xa[m], ra[m], lb[m], xb[m], rb[m], lc[m], xc[m], rc[m]};
-          cx<R> ak = mk<R>(0, 0), am = mk<R>(0, 0);
-#pragma unroll
-          for (int s2 = 0; s2 < 9; ++s2) {
-            ak = fma_s(kr[s2], v[s2], ak);
-            am = fma_s(sc.mtot[s2], v[s2], am);
-          }
+          // three short chains instead of one of nine (latency, not issue, bounds a row)
+          const cx<R> k0 = fma_s(kr[2], v[2], fma_s(kr[1], v[1], kr[0] * v[0]));
+          const cx<R> k1 = fma_s(kr[5], v[5], fma_s(kr[4], v[4], kr[3] * v[3]));
+          const cx<R> k2 = fma_s(kr[8], v[8], fma_s(kr[7], v[7], kr[6] * v[6]));
+          const cx<R> ak = (k0 + k1) + k2;
+          const cx<R> am = fma_s(m3, hb[m], m0 * (ha[m] + hc[m]));
           const cx<R> Ax = fma_c(l, am, ak);
           if (OP == OP_APPLY) {
             y[base] = Ax;
           } else if (OP == OP_RESID) {
             y[base] = bf[f][m] - Ax;
           } else {  // OP_JACOBI
-            const cx<R> diag = fma_s(sc.mtot[4], l, mk<R>(kr[4], R(0)));
-            y[base] = xb[m] + scaled_div(omega, bf[f][m] - Ax, diag);
+            const cx<R> res = bf[f][m] - Ax;
+            if ((sizeof(R) == 8 && sc.dinv != nullptr)) {
+              y[base] = fma_c(sc.dinv[base], res, xb[m]);
+            } else {
+              const cx<R> diag = fma_s(sc.mtot[4], l, mk<R>(kr[4], R(0)));
+              y[base] = xb[m] + scaled_div(omega, res, diag);
+            }
           }
         }
       }
       // roll the rows; refill slot f PF rows ahead
 #pragma unroll
       for (int m = 0; m < MQ; ++m) {
+        ha[m] = hb[m];
+        hb[m] = hc[m];
         xa[m] = xb[m];
         la[m] = lb[m];
         ra[m] = rb[m];
@@ -412,9 +440,33 @@ __global__ void __launch_bounds__(32 * kColWarps) k_stencil_col2(Geo g, StencilC
       cb = cf[f];
       cbr = cnr;
       cf[f] = ldc(row + 2 + PF);
-      buf ^= 1;
     }
   }
+}
+
+// CTAs of a kernel resident on the whole device at once (resident CTAs per
+// SM at 32 kColWarps threads x SMs), cached per kernel and device ordinal.
+template <typename K> int resident_ctas(K kernel) {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const bool cached = dev >= 0 && dev < 64;
+  int v = cached ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (v > 0) return v;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * kColWarps, 0) != cudaSuccess) per_sm = 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+  v = std::max(1, per_sm) * std::max(1, sms);
+  if (cached) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// Rows per strip: as many strips as fill the device's resident CTAs once
+// (a second, partly filled wave of strips would cost a whole strip time),
+// at least 8 rows so that the rows loaded ahead of a strip stay a small part.
+inline int col_rows(int n, int col_groups, int mode_groups, int slots) {
+  const int strips = std::max(1, slots / std::max(1, col_groups * mode_groups));
+  return std::max(8, (n + strips - 1) / strips);
 }
 
 template <typename R, int MQ>
@@ -422,18 +474,12 @@ void stencil_col2_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c
                      cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes, int64_t stride, double omega,
                      cudaStream_t s) {
   const int warps = (g.n + kColOut - 1) / kColOut;
-  const int rows = g.n >= 512 ? 32 : (g.n >= 128 ? 16 : 8);
-  const dim3 grid((warps + kColWarps - 1) / kColWarps, (g.n + rows - 1) / rows, (nmodes + MQ - 1) / MQ);
-  const R om = (R)omega;
-  if (op == OP_APPLY)
-    k_stencil_col2<R, OP_APPLY, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om,
-                                                                    rows);
-  else if (op == OP_RESID)
-    k_stencil_col2<R, OP_RESID, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, om,
-                                                                    rows);
-  else
-    k_stencil_col2<R, OP_JACOBI, MQ><<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride,
-                                                                     om, rows);
+  const int cg = (warps + kColWarps - 1) / kColWarps, mg = (nmodes + MQ - 1) / MQ;
+  auto kern = op == OP_APPLY ? k_stencil_col2<R, OP_APPLY, MQ>
+                             : (op == OP_RESID ? k_stencil_col2<R, OP_RESID, MQ> : k_stencil_col2<R, OP_JACOBI, MQ>);
+  const int rows = col_rows(g.n, cg, mg, resident_ctas(kern));
+  const dim3 grid(cg, (g.n + rows - 1) / rows, mg);
+  kern<<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, (R)omega, rows);
 }
 
 template <typename R, int MQ>
@@ -499,6 +545,17 @@ template <int D> StencilShape default_shape(int64_t nnodes, int nmodes) {
   return StencilShape{mq, kBlock};
 }
 
+// The 2D mass stencil has the tensor form m0 (1, 4, 1) (x) (1, 4, 1) (Q1 on a
+// uniform grid; exact in floating point, the factors being powers of two),
+// which the column-streaming kernel relies on.
+template <typename R> bool mass_separable(const StencilCoefT<R>& sc) {
+  const R m0 = sc.mtot[0];
+  const R w[3] = {R(1), R(4), R(1)};
+  for (int s = 0; s < 9; ++s)
+    if (sc.mtot[s] != m0 * w[s % 3] * w[s / 3]) return false;
+  return true;
+}
+
 // block == 0 selects the shared-memory tile kernel, block == kColBlockCode the
 // column-streaming kernel (both 2D, operations that read x).
 constexpr int kColBlockCode = 64;
@@ -512,7 +569,7 @@ void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const
     else stencil_tile2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     return;
   }
-  if (sh.block == kColBlockCode && D == 2 && op != OP_JACOBI_ZERO) {
+  if (sh.block == kColBlockCode && D == 2 && op != OP_JACOBI_ZERO && mass_separable(sc)) {
     if (sh.mq == 4) stencil_col2_mq<R, 4>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else if (sh.mq == 2) stencil_col2_mq<R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else stencil_col2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
@@ -1528,6 +1585,18 @@ void launch_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2
 }
 
 template <typename R>
+void launch_jacobi_dinv(const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* lam, double omega,
+                        int nmodes, int64_t stride, cx<R>* dinv, cudaStream_t s) {
+  count(1);
+  StencilCoefT<R> sc0 = sc;
+  sc0.dinv = nullptr;
+  const dim3 grid(blocks_for(g.nnodes), nmodes);
+  if (g.d == 1) k_jacobi_dinv<1, R><<<grid, kBlock, 0, s>>>(g, sc0, c2, lam, (R)omega, stride, dinv);
+  else if (g.d == 2) k_jacobi_dinv<2, R><<<grid, kBlock, 0, s>>>(g, sc0, c2, lam, (R)omega, stride, dinv);
+  else k_jacobi_dinv<3, R><<<grid, kBlock, 0, s>>>(g, sc0, c2, lam, (R)omega, stride, dinv);
+}
+
+template <typename R>
 void launch_restrict(const Geo& gf, const Geo& gc, const cx<R>* rf, cx<R>* bc, const CocgScal* scal, int nmodes,
                      int64_t sf, int64_t scs, cudaStream_t s) {
   count(1);
@@ -1950,6 +2019,8 @@ void note_launches(int k) { count(k); }
 #define ST_INST(R)                                                                                                   \
   template void launch_stencil<R>(int, const Geo&, const StencilCoefT<R>&, const R*, const cx<R>*, const cx<R>*, cx<R>*, \
                                   const cx<R>*, const CocgScal*, int, int64_t, double, cudaStream_t);                \
+  template void launch_jacobi_dinv<R>(const Geo&, const StencilCoefT<R>&, const R*, const cx<R>*, double, int,      \
+                                      int64_t, cx<R>*, cudaStream_t);                                                \
   template void launch_restrict<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,      \
                                    int64_t, cudaStream_t);                                                           \
   template void launch_prolong_add<R>(const Geo&, const Geo&, const cx<R>*, cx<R>*, const CocgScal*, int, int64_t,   \

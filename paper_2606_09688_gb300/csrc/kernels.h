@@ -27,6 +27,12 @@ void launch_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2
                     const cx<R>* b, cx<R>* y, const cx<R>* lam, const CocgScal* scal, int nmodes,
                     int64_t stride, double omega, cudaStream_t s);
 
+// dinv_q = omega / diag(K(c2) + lam_q M) of a level for every mode (mode-major,
+// vectors at q * stride), for the Jacobi sweeps through StencilCoefT::dinv.
+template <typename R>
+void launch_jacobi_dinv(const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* lam, double omega,
+                        int nmodes, int64_t stride, cx<R>* dinv, cudaStream_t s);
+
 // Multigrid transfers between level gf (fine) and gc = coarse (N/2).
 template <typename R>
 void launch_restrict(const Geo& gf, const Geo& gc, const cx<R>* rf, cx<R>* bc, const CocgScal* scal, int nmodes,

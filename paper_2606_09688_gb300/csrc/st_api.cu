@@ -990,6 +990,8 @@ st_status ccheck(Component& c, const char* where) {
 // the handle's stream), so that those of different components overlap with
 // each other and with the host work of the components set up after it; the
 // zero-pivot flag they leave in c.cerr is read at the end of st_setup.
+double omega_of(int d);
+
 template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   Work<R>& w = work_of<R>(c);
   if (w.ready) return ST_OK;
@@ -1037,6 +1039,19 @@ template <typename R> st_status prepare_work(st_handle* h, Component& c) {
   ST_CUDA(h, cudaStreamWaitEvent(c.cs, h->entry_ev, 0));
   launch_band_form<R>(c.Kb, c.Mb, c.lamP64, w.band, c.bl, c.nsel, c.cs);
   launch_band_factor<R>(w.band, w.bandG, c.bl, c.nsel, c.cerr, c.cs);
+  if constexpr (sizeof(R) == 8) {
+    // FP64 sweeps are bound by the FP64 pipe: the damped inverse diagonal of
+    // every smoothed level and mode is formed once (the complex reciprocal is
+    // about a fifth of a sweep's FP64 operations); FP32 sweeps, bound by
+    // memory, keep forming it on the fly
+    for (int l = 0; !c.direct && l + 1 < (int)c.mg.size(); ++l) {
+      MGLevel& lv = c.mg[l];
+      cx<R>* dv = h->alloc<cx<R>>((size_t)c.nsel * lv.geo.nnodes);
+      ST_NEED(h, dv);
+      launch_jacobi_dinv<R>(lv.geo, lv.sc, lv.c2d, c.lamP64, omega_of(lv.geo.d), c.nsel, lv.geo.nnodes, dv, c.cs);
+      lv.sc.dinv = dv;
+    }
+  }
   c.bk = blk_layout(c.bl);
   if (c.bk.rt > 0 && (c.direct || c.bl.nrow > kMaxDenseCoarse)) {
     // banded solves in every step: blocked solve with precomputed block inverses
