@@ -537,6 +537,11 @@ def run_ours(args):
               "components_alone_ms": {p: r["comp_ms"] for p, r in results.items()},
               "cpu_baseline": cpu, "e2e": e2e, "alu_peaks": alu, "subresults": subs,
               "clocks": head["clocks"], "launches": {p: r["launches"] for p, r in results.items()}}
+    try:
+        from paper_2606_09688_gb300.st import tuned_shapes
+        detail["tuned_shapes"] = tuned_shapes()
+    except Exception as e:  # diagnostics only
+        detail["tuned_shapes"] = str(e)
     write_detail(detail)
     print(json.dumps(line, separators=(",", ":")), flush=True)
 

@@ -358,6 +358,22 @@ __global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 
     cbr = __shfl_down_sync(0xffffffffu, cb, 1);
   }
   const int rend = min(r0 + rows, n);
+  // in the row loop every access of a mode's vectors is at one 32-bit node
+  // offset (row n + ix, advanced by n per row) from the mode's base
+  // pointer, and the refills at fixed distances ahead of it
+  bool okx[MQ], okb[MQ];
+  cx<R>* yq[MQ];
+  cx<R> lq[MQ];
+#pragma unroll
+  for (int m = 0; m < MQ; ++m) {
+    okx[m] = act[m] && colok;
+    okb[m] = OP != OP_APPLY && act[m] && writer;
+    yq[m] = y + (int64_t)(act[m] ? q0 + m : 0) * stride;
+    lq[m] = act[m] ? lam[q0 + m] : zero;
+  }
+  const int dx = (2 + PF) * n, dbn = PF * n;
+  int oy = r0 * n + ix;
+  int oc = (r0 + 2 + PF) * N + ix;
   // rows in groups of PF: queue slot f is refilled right after it is used,
   // with no register moves of loads still in flight
   for (int row0 = r0; row0 < rend; row0 += PF) {
@@ -390,13 +406,10 @@ __global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 
         kr[8] = c11;
 #pragma unroll
         for (int s2 = 0; s2 < 9; ++s2) kr[s2] *= sc.ke[s2];
-        const int64_t a = (int64_t)row * n + ix;
 #pragma unroll
         for (int m = 0; m < MQ; ++m) {
           if (!act[m]) continue;
-          const int q = q0 + m;
-          const cx<R> l = lam[q];
-          const int64_t base = (int64_t)q * stride + a;
+          const cx<R> l = lq[m];
           const cx<R> v[9] = {la[m], xa[m], ra[m], lb[m], xb[m], rb[m], lc[m], xc[m], rc[m]};
           // three short chains instead of one of nine (latency, not issue, bounds a row)
           const cx<R> k0 = fma_s(kr[2], v[2], fma_s(kr[1], v[1], kr[0] * v[0]));
@@ -406,16 +419,16 @@ __global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 
           const cx<R> am = fma_s(m3, hb[m], m0 * (ha[m] + hc[m]));
           const cx<R> Ax = fma_c(l, am, ak);
           if (OP == OP_APPLY) {
-            y[base] = Ax;
+            yq[m][oy] = Ax;
           } else if (OP == OP_RESID) {
-            y[base] = bf[f][m] - Ax;
+            yq[m][oy] = bf[f][m] - Ax;
           } else {  // OP_JACOBI
             const cx<R> res = bf[f][m] - Ax;
             if ((sizeof(R) == 8 && sc.dinv != nullptr)) {
-              y[base] = fma_c(sc.dinv[base], res, xb[m]);
+              yq[m][oy] = fma_c(sc.dinv[(int64_t)(q0 + m) * stride + oy], res, xb[m]);
             } else {
               const cx<R> diag = fma_s(sc.mtot[4], l, mk<R>(kr[4], R(0)));
-              y[base] = xb[m] + scaled_div(omega, res, diag);
+              yq[m][oy] = xb[m] + scaled_div(omega, res, diag);
             }
           }
         }
@@ -432,22 +445,26 @@ __global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 
         lb[m] = lc[m];
         rb[m] = rc[m];
         xc[m] = xf[f][m];
-        xf[f][m] = ldx(m, row + 2 + PF);
-        bf[f][m] = ldb(m, row + PF);
+        xf[f][m] = (okx[m] && row + 2 + PF < n) ? xq[m][oy + dx] : zero;
+        bf[f][m] = (okb[m] && row + PF < n) ? bq[m][oy + dbn] : zero;
       }
       ca = cb;
       car = cbr;
       cb = cf[f];
       cbr = cnr;
-      cf[f] = ldc(row + 2 + PF);
+      cf[f] = (cellok && row + 2 + PF < N) ? c2[oc] : R(0);
+      oy += n;
+      oc += N;
     }
   }
 }
 
-// CTAs of a kernel resident on the whole device at once (resident CTAs per
-// SM at 32 kColWarps threads x SMs), cached per kernel and device ordinal.
-template <typename K> int resident_ctas(K kernel) {
+// CTAs of a column-streaming kernel resident on the whole device at once
+// (resident CTAs per SM at 32 kColWarps threads x SMs), cached per kernel
+// (the template arguments) and device ordinal.
+template <typename R, int OP, int MQ> int resident_ctas() {
   static std::atomic<int> cache[64];
+  auto kernel = k_stencil_col2<R, OP, MQ>;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
   const bool cached = dev >= 0 && dev < 64;
@@ -477,7 +494,9 @@ void stencil_col2_mq(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c
   const int cg = (warps + kColWarps - 1) / kColWarps, mg = (nmodes + MQ - 1) / MQ;
   auto kern = op == OP_APPLY ? k_stencil_col2<R, OP_APPLY, MQ>
                              : (op == OP_RESID ? k_stencil_col2<R, OP_RESID, MQ> : k_stencil_col2<R, OP_JACOBI, MQ>);
-  const int rows = col_rows(g.n, cg, mg, resident_ctas(kern));
+  const int slots = op == OP_APPLY ? resident_ctas<R, OP_APPLY, MQ>()
+                                   : (op == OP_RESID ? resident_ctas<R, OP_RESID, MQ>() : resident_ctas<R, OP_JACOBI, MQ>());
+  const int rows = col_rows(g.n, cg, mg, slots);
   const dim3 grid(cg, (g.n + rows - 1) / rows, mg);
   kern<<<grid, 32 * kColWarps, 0, s>>>(g, sc, c2, x, b, y, lam, scal, nmodes, stride, (R)omega, rows);
 }
@@ -1341,7 +1360,11 @@ __global__ void __launch_bounds__(kBlock) k_comb_level(int j, const double* __re
 // ------------------------------------------------- dense coarse-level solve
 // x_q = Ainv_q b_q: b_q staged in shared memory, one warp per row (coalesced
 // row reads, lanes over columns), warp-shuffle reduction of the dot product.
-constexpr int kDenseRowsPerBlock = 32;
+// One row per warp and CTA of 8 warps: a coarse grid of 961 unknowns and a few
+// modes gives several hundred CTAs, spread evenly over the SMs (with 32 rows
+// per CTA the ~150 CTAs left a few SMs with two, and the FP64 launch at half
+// of the FP64 rate).
+constexpr int kDenseRowsPerBlock = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_dense_mv(const cx<R>* __restrict__ Ainv, int n,
@@ -1359,15 +1382,30 @@ __global__ void __launch_bounds__(kBlock) k_dense_mv(const cx<R>* __restrict__ A
   const int r1 = min(n, (int)(blockIdx.x + 1) * kDenseRowsPerBlock);
   for (int r = blockIdx.x * kDenseRowsPerBlock + warp; r < r1; r += kBlock / 32) {
     const cx<R>* row = Aq + (int64_t)r * n;
-    R re = R(0), im = R(0);
-    for (int c = lane; c < n; c += 32) {
-      const cx<R> a = row[c], v = bs[c];
-      re = fma(a.re, v.re, fma(-a.im, v.im, re));
-      im = fma(a.re, v.im, fma(a.im, v.re, im));
+    // four independent partial sums: four row loads in flight per warp (one
+    // load per iteration left the kernel waiting on memory latency)
+    R re[4] = {R(0), R(0), R(0), R(0)}, im[4] = {R(0), R(0), R(0), R(0)};
+    int c = lane;
+    for (; c + 96 < n; c += 128) {
+      cx<R> a[4], v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = row[c + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = bs[c + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        re[u] = fma(a[u].re, v[u].re, fma(-a[u].im, v[u].im, re[u]));
+        im[u] = fma(a[u].re, v[u].im, fma(a[u].im, v[u].re, im[u]));
+      }
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) x[(int64_t)q * vstride + r] = mk<R>(re, im);
+    for (; c < n; c += 32) {
+      const cx<R> a = row[c], v = bs[c];
+      re[0] = fma(a.re, v.re, fma(-a.im, v.im, re[0]));
+      im[0] = fma(a.re, v.im, fma(a.im, v.re, im[0]));
+    }
+    const R rs = warp_sum((re[0] + re[1]) + (re[2] + re[3]));
+    const R is = warp_sum((im[0] + im[1]) + (im[2] + im[3]));
+    if (lane == 0) x[(int64_t)q * vstride + r] = mk<R>(rs, is);
   }
 }
 

@@ -1133,8 +1133,10 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
   if constexpr (sizeof(R) == 8) {
     // FP64 inner solves are bound by the FP64 pipe: one sweep before and one
     // after the coarse correction (V(1,1)) costs fewer FP64 operations per
-    // solve than V(2,2) despite one or two more Krylov iterations
-    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 2 * cs + cb, m * n * 30.0,
+    // solve than V(2,2) despite one or two more Krylov iterations.  The sweeps
+    // read the damped inverse diagonal (StencilCoefT::dinv): 16 more bytes and
+    // one complex product per node and mode instead of the division
+    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs, m * n * 6.0,
          launch_stencil<R>(OP_JACOBI_ZERO, lv.geo, coef_of<R>(lv), c2, nullptr, b, xb, lam, c.scal, c.nsel, n, om, s));
     PROF(h, s, KC_MG_RESID, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 2.0),
          launch_stencil<R>(OP_RESID, lv.geo, coef_of<R>(lv), c2, xb, b, rtmp, lam, c.scal, c.nsel, n, om, s));
@@ -1143,7 +1145,7 @@ cx<R>* vcycle(st_handle* h, Component& c, int l, const cx<R>* b, cx<R>* xa, cx<R
     cx<R>* xc = vcycle<R>(h, c, l + 1, w.bl[l + 1], w.xa[l + 1], w.xb[l + 1], w.rl[l + 1]);
     PROF(h, s, KC_PROLONG, (int64_t)(n), m * (2.0 * n + nc) * cs, m * n * 4.0 * (1 << lv.geo.d),
          launch_prolong_add<R>(lv.geo, lc.geo, xc, xb, c.scal, c.nsel, n, lc.geo.nnodes, s));
-    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 3 * cs + cb, m * n * (fl + 30.0),
+    PROF(h, s, KC_JACOBI, (int64_t)(n), m * n * 4 * cs + cb, m * n * (fl + 8.0),
          launch_stencil<R>(OP_JACOBI, lv.geo, coef_of<R>(lv), c2, xb, b, xa, lam, c.scal, c.nsel, n, om, s));
     return xa;
   }
