@@ -297,8 +297,9 @@ st_status st_profile_read(st_handle* h, st_kernel_stat* out, int max_out, int* n
 /* Launch shapes chosen by the stencil autotuner so far in this process:
  * 7 ints per entry (operation 0 apply / 1 residual / 2 Jacobi / 3 first
  * Jacobi sweep, dimension, element size in bytes, grid nodes, time modes,
- * modes per thread, threads per CTA, or 0 for the 2D shared-memory tile
- * kernel, or 64 for the 2D column-streaming kernel), at most max_entries written to out
+ * modes per thread (1, 2 or 4; 3 with the column-streaming kernel only),
+ * threads per CTA, or 0 for the 2D shared-memory tile kernel, or 64 for the
+ * 2D column-streaming kernel), at most max_entries written to out
  * (may be NULL); *n_out = the number of entries. */
 st_status st_tuned_shapes(int* out, int max_entries, int* n_out);
 /* Pin the launch shape of one (operation, dimension, element size, grid

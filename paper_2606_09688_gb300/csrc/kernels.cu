@@ -286,13 +286,13 @@ __global__ void __launch_bounds__(256) k_stencil_tile2(Geo g, StencilCoefT<R> sc
 // requests in flight instead of waiting one load latency per row.
 constexpr int kColWarps = 4, kColOut = 30;
 template <typename R, int OP, int MQ>
-__global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 6 : 1) k_stencil_col2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
+__global__ void __launch_bounds__(32 * kColWarps, sizeof(R) == 4 && MQ == 1 ? 5 : 1) k_stencil_col2(Geo g, StencilCoefT<R> sc, const R* __restrict__ c2,
                                                                   const cx<R>* __restrict__ x,
                                                                   const cx<R>* __restrict__ b, cx<R>* __restrict__ y,
                                                                   const cx<R>* __restrict__ lam,
                                                                   const CocgScal* __restrict__ scal, int nmodes,
                                                                   int64_t stride, R omega, int rows) {
-  constexpr int PF = MQ >= 4 ? 1 : (MQ == 2 ? 2 : 3);  // rows of loads in flight ahead of the computed row
+  constexpr int PF = MQ >= 4 ? 1 : (MQ >= 2 ? 2 : 4);  // rows of loads in flight ahead of the computed row
   const int n = g.n, N = g.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ix = (blockIdx.x * kColWarps + warp) * kColOut - 1 + lane;
@@ -590,6 +590,7 @@ void stencil_launch_shape(int op, const Geo& g, const StencilCoefT<R>& sc, const
   }
   if (sh.block == kColBlockCode && D == 2 && op != OP_JACOBI_ZERO && mass_separable(sc)) {
     if (sh.mq == 4) stencil_col2_mq<R, 4>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
+    else if (sh.mq == 3) stencil_col2_mq<R, 3>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else if (sh.mq == 2) stencil_col2_mq<R, 2>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     else stencil_col2_mq<R, 1>(op, g, sc, c2, x, b, y, lam, scal, nmodes, stride, omega, s);
     return;
@@ -612,7 +613,8 @@ void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* 
 }
 
 // Autotuner: time every candidate shape (modes per thread 1, 2, 4 (1, 2 in
-// 3D) x block 128, 256, 512, and in 2D the shared-memory tile kernel) of one
+// 3D) x block 128, 256, 512, and in 2D the shared-memory tile and the
+// column-streaming kernels, the latter also with 3 modes per thread) of one
 // stencil operation on the caller's
 // buffers with CUDA events, the median of three launches each after one
 // untimed launch, and keep the fastest for this (operation, dimension,
@@ -621,7 +623,7 @@ void stencil_dispatch(int op, const Geo& g, const StencilCoefT<R>& sc, const R* 
 template <int D, typename R>
 float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2, const cx<R>* x, const cx<R>* b,
                    cx<R>* y, const cx<R>* lam, int nmodes, int64_t stride, double omega, cudaStream_t s) {
-  const int mqs[3] = {1, 2, 4};
+  const int mqs[4] = {1, 2, 3, 4};  // 3: column-streaming kernel only (three-mode components)
   const int blocks[5] = {128, 256, 512, 0, kColBlockCode};  // 0: shared-memory tiles, 64: column streaming (2D)
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
@@ -636,6 +638,7 @@ float stencil_tune(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
     if (mq > 1 && mq > 2 * nmodes) continue;
     for (int bk : blocks) {
       if ((bk == 0 || bk == kColBlockCode) && (D != 2 || op == OP_JACOBI_ZERO)) continue;
+      if (mq == 3 && bk != kColBlockCode) continue;
       const StencilShape sh{mq, bk};
       float t[3];
       stencil_launch_shape<D, R>(op, g, sc, c2, x, b, y, lam, nullptr, nmodes, stride, omega, sh, s);
@@ -2022,7 +2025,8 @@ float tune_stencil(int op, const Geo& g, const StencilCoefT<R>& sc, const R* c2,
 
 bool set_stencil_shape(int op, int d, int rsize, int64_t nnodes, int nmodes, int mq, int block) {
   if (op < 0 || op > 3 || d < 1 || d > 3 || (rsize != 4 && rsize != 8) || nnodes < 1 || nmodes < 1) return false;
-  if (mq != 1 && mq != 2 && mq != 4) return false;
+  if (mq != 1 && mq != 2 && mq != 3 && mq != 4) return false;
+  if (mq == 3 && block != kColBlockCode) return false;
   if (d == 3 && mq == 4) return false;
   if (block != 0 && block != kColBlockCode && block != 128 && block != 256 && block != 512) return false;
   if ((block == 0 || block == kColBlockCode) && (d != 2 || op == OP_JACOBI_ZERO)) return false;

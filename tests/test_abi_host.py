@@ -203,6 +203,8 @@ def test_tuned_shape_pinning_validates_the_shape():
     assert good in tuned_shapes()
     set_tuned_shape(dict(good, block=64))
     assert dict(good, block=64) in tuned_shapes()
+    set_tuned_shape(dict(good, block=64, modes_per_thread=3))   # three modes per thread: column kernel only
+    assert dict(good, block=64, modes_per_thread=3) in tuned_shapes()
     for bad in (dict(good, modes_per_thread=3), dict(good, block=96), dict(good, d=3, block=0),
                 dict(good, d=3, block=64), dict(good, op=3, block=64),
                 dict(good, op=3, block=0), dict(good, d=3, modes_per_thread=4, block=256),

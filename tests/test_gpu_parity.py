@@ -280,18 +280,20 @@ def test_autotuned_launch_shapes_keep_the_results():
     shapes = tuned_shapes()
     assert any(e["nodes"] == 127 * 127 for e in shapes)
     for e in shapes:
-        assert e["modes_per_thread"] in (1, 2, 4) and e["block"] in (0, 64, 128, 256, 512)
+        assert e["modes_per_thread"] in (1, 2, 3, 4) and e["block"] in (0, 64, 128, 256, 512)
+        assert e["modes_per_thread"] != 3 or e["block"] == 64
     for kernel in (0, 64):        # the shared-memory tile kernel, then the column-streaming kernel
         pinned = 0
         for e in shapes:
             if e["d"] == 2 and e["op"] != 3:
-                set_tuned_shape(dict(e, block=kernel))
+                mq = 2 if (kernel == 0 and e["modes_per_thread"] == 3) else e["modes_per_thread"]
+                set_tuned_shape(dict(e, block=kernel, modes_per_thread=mq))
                 pinned += 1
         assert pinned > 0
         for prec in (ST_FP64, ST_FP32_IR):
             assert _rel(run(prec, -1), ref) < (TOL64 if prec == ST_FP64 else TOL32), kernel
     with pytest.raises(StError):
-        set_tuned_shape(dict(shapes[0], modes_per_thread=3))
+        set_tuned_shape(dict(shapes[0], modes_per_thread=3, block=128))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
