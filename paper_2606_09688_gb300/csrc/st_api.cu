@@ -35,10 +35,20 @@
 #include "band.h"
 #include "host_math.h"
 #include "kernels.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace st;
 
 namespace {
+
+// NVTX range of one phase of an entry point (visible to profilers that
+// record NVTX, e.g. ncu --nvtx; a no-op without one).
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+};
 
 constexpr int kMaxDirectRows = 32768;  // largest grid solved by the banded direct method (3D: 31^3)
 constexpr int64_t kCoarseFloor = 1024;     // multigrid coarsening stops at the largest grid of at most this size
@@ -2090,6 +2100,7 @@ struct StepTrace {
 extern "C" {
 
 st_status st_setup(const st_problem* problem, const st_options* options, st_handle** out) {
+  Phase phase_("st_setup");
   if (out == nullptr || problem == nullptr) return fail(nullptr, ST_ERR_ARG, "null argument");
   *out = nullptr;
   SetupTrace trace;
@@ -2292,6 +2303,7 @@ st_status st_component(const st_handle* h, int k, st_component_info* info) {
 }
 
 st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
+  Phase phase_("st_solve_component");
   if (!h) return ST_ERR_ARG;
   ++h->api_seq;
   if (k < -1 || k >= (int)h->comps.size()) return fail(h, ST_ERR_ARG, "component index out of range");
@@ -2300,6 +2312,7 @@ st_status st_solve_component(st_handle* h, int k, st_solve_info* info) {
 }
 
 st_status st_solve_batch(st_handle* const* hs, int n, int max_threads, st_solve_info* info) {
+  Phase phase_("st_solve_batch");
   if (!hs || n < 1 || max_threads < 0) return ST_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return ST_ERR_ARG;
@@ -2386,6 +2399,7 @@ st_status st_combine(st_handle* h, int jx_star, int jt_star, double* out_dev) {
 }
 
 st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* comps, int ncomp, double* out_dev) {
+  Phase phase_("st_combine");
   if (!h || !out_dev || !comps || ncomp < 1) return ST_ERR_ARG;
   ++h->api_seq;
   if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
@@ -2406,6 +2420,7 @@ st_status st_combine_subset(st_handle* h, int jx_star, int jt_star, const int* c
 }
 
 st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_dev, st_solve_info* info) {
+  Phase phase_("st_solve_combine");
   if (!h || !out_dev) return ST_ERR_ARG;
   ++h->api_seq;
   if (jx_star < 1 || jt_star < 0 || jx_star > 14 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target level");
@@ -2561,6 +2576,7 @@ st_status st_solve_combine(st_handle* h, int jx_star, int jt_star, double* out_d
 }
 
 st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int n_rec, double* out_dev) {
+  Phase phase_("st_receiver_values");
   if (!h || !x_rec || !out_dev || n_rec < 1) return ST_ERR_ARG;
   ++h->api_seq;
   if (jt_star < 0 || jt_star > 14) return fail(h, ST_ERR_ARG, "bad target time level");
@@ -2575,6 +2591,7 @@ st_status st_receiver_values(st_handle* h, int jt_star, const double* x_rec, int
 
 st_status st_misfit_gradient(st_handle* h, int jt_star, const double* x_rec, int n_rec, const double* d_obs_dev,
                              int jp, double* J_out, double* dc2_dev, double* dg_dev, st_solve_info* info) {
+  Phase phase_("st_misfit_gradient");
   if (!h || !x_rec || !d_obs_dev || n_rec < 1 || !J_out || !dc2_dev || !dg_dev) return ST_ERR_ARG;
   ++h->api_seq;
   const st_problem& p = h->prob;
@@ -2647,6 +2664,7 @@ st_status st_tuned_shapes(int* out, int max_entries, int* n_out) {
 }
 
 st_status st_energy(st_handle* h, const double* times, int ntimes, int jx_eval, double* energy_out) {
+  Phase phase_("st_energy");
   if (!h || !times || !energy_out || ntimes < 1) return ST_ERR_ARG;
   ++h->api_seq;
   const st_problem& p = h->prob;
