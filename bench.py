@@ -518,7 +518,7 @@ def run_ours(args):
             "sample": cpu["sample_short"]},
         "e2e": None if e2e is None else {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step",
                                                             "d2h_bytes_per_step")},
-        "backward_error": sig(head["backward_error"], 2),
+        "backward_error": sig(head["backward_error"], 2), "sweeps": head["sweeps"], "inner_iters": head["inner_iters"],
     }
     if line["e2e"]:
         line["e2e"]["value"] = sig(line["e2e"]["value"])
@@ -527,6 +527,7 @@ def run_ours(args):
             continue
         rr = roofline(r["stats"], hbm, hbm_src, prec, alu)
         line[prec] = {"value": sig(r["value"]), "ms_per_step": sig(r["ms"]), "backward_error": sig(r["backward_error"], 2),
+                      "sweeps": r["sweeps"], "inner_iters": r["inner_iters"],
                       "roofline_frac": sig(rr["frac"], 3) if rr else None}
     for name, sub in subs.items():
         line[name] = {"value": sig(sub["value"]), "ms_per_step": sig(sub["ms_per_step"]),

@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kBlock) k_reduce_partial(const cx<R>* __restri
 
 template <int WHICH>
 __global__ void k_reduce_final(CocgScal* __restrict__ scal, const double* __restrict__ part, int nblk, double tol,
-                               int max_iter) {
+                               int max_iter, const double* __restrict__ tolp = nullptr) {
   const int q = blockIdx.x;
   CocgScal& S = scal[q];
   if (WHICH != RED_BB && !S.active) return;
@@ -853,7 +853,7 @@ __global__ void k_reduce_final(CocgScal* __restrict__ scal, const double* __rest
     if (!finite) {
       S.status = 7;
       S.active = 0;
-    } else if (v.re <= tol * tol * S.bb) {
+    } else if (v.re <= (tolp != nullptr ? tolp[0] * tolp[0] : tol * tol) * S.bb) {
       S.active = 0;
     } else if (S.iters >= max_iter) {
       S.status = 4;
@@ -1678,10 +1678,18 @@ void launch_dot(int which, const cx<R>* a, const cx<R>* b, CocgScal* scal, doubl
 
 template <typename R>
 void launch_update_xr(cx<R>* x, cx<R>* r, const cx<R>* p, const cx<R>* w, CocgScal* scal, double* part,
-                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s) {
+                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s,
+                      const double* tolp) {
   count(2);
   k_update_xr<R><<<dim3(kRedBlocks, nmodes), kBlock, 0, s>>>(x, r, p, w, scal, part, n, stride);
-  k_reduce_final<RED_RR><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter);
+  k_reduce_final<RED_RR><<<nmodes, 256, 0, s>>>(scal, part, kRedBlocks, tol, max_iter, tolp);
+}
+
+__global__ void k_set_scalar(double* __restrict__ p, double v) { p[0] = v; }
+
+void launch_set_scalar(double* p, double v, cudaStream_t s) {
+  count(1);
+  k_set_scalar<<<1, 1, 0, s>>>(p, v);
 }
 
 template <typename R>
@@ -1845,7 +1853,8 @@ __global__ void k_cocg_continue(const CocgScal* __restrict__ scal, int nmodes, c
 }
 
 __global__ void k_refine_init(RefineRec* __restrict__ rec, const double* __restrict__ fn2,
-                              cudaGraphConditionalHandle h) {
+                              cudaGraphConditionalHandle h, InnerTol it) {
+  if (it.tol != nullptr) it.tol[0] = it.base;
   const double f = fn2[0];
   RefineRec r{};
   r.eta_prev = 1e300;
@@ -1858,7 +1867,7 @@ __global__ void k_refine_init(RefineRec* __restrict__ rec, const double* __restr
 __global__ void k_refine_decide(RefineRec* __restrict__ rec, const double* __restrict__ nrm2,
                                 const double* __restrict__ fn2, double snorm, double tol, int max_sweeps,
                                 const CocgScal* __restrict__ scal, int nsel, const int* __restrict__ cerr,
-                                cudaGraphConditionalHandle h) {
+                                cudaGraphConditionalHandle h, InnerTol itol) {
   int it = 0, worst = 0;  // worst: 2 = an iteration limit, 1 = another non-zero status word
   if (scal != nullptr)
     for (int q = threadIdx.x; q < nsel; q += 32) {
@@ -1886,6 +1895,7 @@ __global__ void k_refine_decide(RefineRec* __restrict__ rec, const double* __res
   r.eta_prev = eta;
   r.status = st;
   *rec = r;
+  if (itol.tol != nullptr && itol.adaptive) itol.tol[0] = next_inner_tol(itol.base, tol, eta, itol.amp);
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
@@ -1908,16 +1918,17 @@ void launch_cocg_continue(const CocgScal* scal, int nmodes, cudaGraphConditional
   k_cocg_continue<<<1, 128, 0, s>>>(scal, nmodes, handle, bodies);
 }
 
-void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, cudaStream_t s) {
+void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, InnerTol it,
+                        cudaStream_t s) {
   count(1);
-  k_refine_init<<<1, 1, 0, s>>>(rec, fn2, h);
+  k_refine_init<<<1, 1, 0, s>>>(rec, fn2, h, it);
 }
 
 void launch_refine_decide(RefineRec* rec, const double* nrm2, const double* fn2, double snorm, double tol,
                           int max_sweeps, const CocgScal* scal, int nsel, const int* cerr,
-                          cudaGraphConditionalHandle h, cudaStream_t s) {
+                          cudaGraphConditionalHandle h, InnerTol it, cudaStream_t s) {
   count(1);
-  k_refine_decide<<<1, 32, 0, s>>>(rec, nrm2, fn2, snorm, tol, max_sweeps, scal, nsel, cerr, h);
+  k_refine_decide<<<1, 32, 0, s>>>(rec, nrm2, fn2, snorm, tol, max_sweeps, scal, nsel, cerr, h, it);
 }
 
 size_t time_band_smem(int nt) { return (size_t)nt * (7 * sizeof(double) + sizeof(double) + sizeof(int)); }
@@ -2072,7 +2083,7 @@ void note_launches(int k) { count(k); }
   template void launch_dot<R>(int, const cx<R>*, const cx<R>*, CocgScal*, double*, int, int64_t, int64_t, double,    \
                               int, cudaStream_t);                                                                    \
   template void launch_update_xr<R>(cx<R>*, cx<R>*, const cx<R>*, const cx<R>*, CocgScal*, double*, int, int64_t,    \
-                                    int64_t, double, int, cudaStream_t);                                             \
+                                    int64_t, double, int, cudaStream_t, const double*);                              \
   template void launch_update_p<R>(cx<R>*, const cx<R>*, const CocgScal*, int, int64_t, int64_t, int, cudaStream_t);      \
   template void launch_fwd_transform<R>(const cx<double>*, const double*, cx<R>*, int, int, int64_t, cudaStream_t);  \
   template void launch_back_transform<R>(const cx<double>*, const double*, const cx<R>*, double*, int, int, int64_t, \

@@ -49,8 +49,29 @@ template <typename R>
 void launch_dot(int which, const cx<R>* a, const cx<R>* b, CocgScal* scal, double* part, int nmodes, int64_t n,
                 int64_t stride, double tol, int max_iter, cudaStream_t s);
 template <typename R>
+// The convergence test rr <= tol^2 bb takes tol from tolp[0] (device) when tolp is set.
 void launch_update_xr(cx<R>* x, cx<R>* r, const cx<R>* p, const cx<R>* w, CocgScal* scal, double* part,
-                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s);
+                      int nmodes, int64_t n, int64_t stride, double tol, int max_iter, cudaStream_t s,
+                      const double* tolp = nullptr);
+void launch_set_scalar(double* p, double v, cudaStream_t s);
+
+// Inner (COCG) tolerance of the refinement sweeps.  The first sweep solves to
+// `base`; with FP64 inner solves a later sweep only has to reduce the
+// space-time backward error eta by target / eta, and a relative modal
+// residual eps changes the space-time residual by at most amp eps (amp from
+// the conditioning of the time eigenbasis), so it solves to
+// eps = 0.05 target / (eta amp), kept within [base, 1e-2].
+__host__ __device__ inline double next_inner_tol(double base, double target, double eta, double amp) {
+  if (!(eta > 0.0) || !(eta < 1e300)) return base;
+  const double t = 0.05 * target / (eta * amp);
+  return fmin(1e-2, fmax(base, t));
+}
+struct InnerTol {
+  double* tol;    // device scalar read by the COCG convergence test (null: fixed tolerance)
+  double base;    // tolerance of the first sweep
+  double amp;     // residual amplification bound of the transforms
+  int adaptive;   // 0: every sweep solves to base
+};
 template <typename R>
 void launch_update_p(cx<R>* p, const cx<R>* z, const CocgScal* scal, int nmodes, int64_t n, int64_t stride,
                      int first, cudaStream_t s);
@@ -69,14 +90,15 @@ struct RefineRec {
 };
 enum { RR_OK = 0, RR_NUMERIC = 1, RR_ITER_LIMIT = 2, RR_TIMEOUT = 3 };
 // Clears the record; the sweep loop runs when ||F||^2 (fn2[0]) is positive.
-void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_refine_init(RefineRec* rec, const double* fn2, cudaGraphConditionalHandle h, InnerTol it,
+                        cudaStream_t s);
 // After a sweep: nrm2 = (||R||^2, ||U||^2), fn2 = ||F||^2.  Stops on
 // eta = ||R|| / (snorm ||U|| + ||F||) <= tol, when eta no longer halves, after
 // max_sweeps, on a COCG status word (scal may be null), a copy timeout
 // (cerr[0] != 0, may be null) or a non-finite residual.
 void launch_refine_decide(RefineRec* rec, const double* nrm2, const double* fn2, double snorm, double tol,
                           int max_sweeps, const CocgScal* scal, int nsel, const int* cerr,
-                          cudaGraphConditionalHandle h, cudaStream_t s);
+                          cudaGraphConditionalHandle h, InnerTol it, cudaStream_t s);
 
 // Time transforms of the eigenbasis method (FP64 matrices):
 // G[q][a] = sum_i W[q][i] R[i][a];  U[i][a] += sum_q w_q Re(V[i][q] X[q][a]).

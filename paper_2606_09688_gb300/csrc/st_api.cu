@@ -259,6 +259,10 @@ struct Component {
   cudaGraphExec_t g_init = nullptr, g_iter = nullptr;
   int64_t g_init_nodes = 0, g_iter_nodes = 0;
   double fnorm = -1.0;             // ||F|| of the forward right-hand side (constant after setup)
+  // inner tolerance of the current refinement sweep (device scalar read by
+  // the COCG convergence test) and its rule (next_inner_tol)
+  double* itol = nullptr;
+  InnerTol itol_rule{nullptr, 0.0, 1.0, 0};
   // The whole forward solve as one graph (st_options.device_loop > 0): the
   // refinement sweeps in a WHILE node, the COCG loop of a sweep in a nested
   // one; the host reads its record once the call's work is done.
@@ -1182,8 +1186,13 @@ double inner_tol(const st_handle* h, size_t rsize) {
   if (h->opt.inner_tol > 0.0) return h->opt.inner_tol;
   // FP32: each sweep gains about four digits whatever the inner tolerance
   // (the FP32 representation of the correction limits it), so a loose
-  // inner solve costs fewer iterations for the same number of sweeps
-  return rsize == 8 ? 1e-12 : 1e-4;
+  // inner solve costs fewer iterations for the same number of sweeps.
+  // FP64: the first sweep's backward error is about 3e-4 times the inner
+  // tolerance on the multigrid components (3e-16 at 1e-12, 30 times below
+  // the default target 1e-14), so 1e-11 still meets the target in one sweep;
+  // where it does not, the next sweep solves only as far as needed
+  // (next_inner_tol)
+  return rsize == 8 ? 1e-11 : 1e-4;
 }
 
 // COCG start: x = 0, r = g, z = B r, rho = r . z, p = z.
@@ -1221,7 +1230,7 @@ template <typename R> void cocg_iteration(st_handle* h, Component& c) {
   PROF(h, s, KC_REDUCE, (int64_t)(n), m * n * 2 * cs, m * n * 8.0,
        launch_dot<R>(0, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
   PROF(h, s, KC_UPDATE, (int64_t)(n), m * n * 6 * cs, m * n * 12.0,
-       launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
+       launch_update_xr<R>(w.X, w.Rr, w.P, w.Wv, c.scal, c.part, c.nsel, n, n, tol, max_iter, s, c.itol));
   cx<R>* z = vcycle<R>(h, c, 0, w.Rr, w.T0, w.Z, w.R0);
   PROF(h, s, KC_REDUCE, (int64_t)(n), m * n * 2 * cs, m * n * 8.0,
        launch_dot<R>(1, w.Rr, z, c.scal, c.part, c.nsel, n, n, tol, max_iter, s));
@@ -1455,6 +1464,10 @@ st_status solve_one(st_handle* h, Component& c, const SolveIO& io, bool adjoint)
   const double* Rin = io.rhs;
   for (int sw = 0; sw < max_sweeps; ++sw) {
     int iters = 0;
+    if (c.itol != nullptr) {
+      const InnerTol& r = c.itol_rule;
+      launch_set_scalar(c.itol, (sw > 0 && r.adaptive) ? next_inner_tol(r.base, tol, eta, r.amp) : r.base, c.cs);
+    }
     if (c.method == 1) {
       s = sweep_space_eig(h, c, io, Rin);
     } else if (c.inner64) {
@@ -1581,7 +1594,7 @@ template <typename R> st_status capture_solve_graph(st_handle* h, Component& c) 
     cudaMemsetAsync(io.sol, 0, (size_t)n * sizeof(double), c.cs);
     cudaMemcpyAsync(c.Rv, io.rhs, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c.cs);
     launch_norm2(io.rhs, n, c.cpart, c.fn2, c.cs);
-    launch_refine_init(c.rec, c.fn2, hs, c.cs);
+    launch_refine_init(c.rec, c.fn2, hs, c.itol_rule, c.cs);
     ok(capture_add_while(c.cs, hs, &sweep), "sweep node");
     cudaGraph_t out = nullptr;
     ok(cudaStreamEndCapture(c.cs, &out), "prologue capture end");
@@ -1613,7 +1626,7 @@ template <typename R> st_status capture_solve_graph(st_handle* h, Component& c) 
     launch_norm2(c.Rv, n, c.cpart, c.cscalar, c.cs);
     launch_norm2(io.sol, n, c.cpart, c.cscalar + 1, c.cs);
     launch_refine_decide(c.rec, c.cscalar, c.fn2, c.Snorm, tol, max_sweeps, iterative ? c.scal : nullptr, c.nsel,
-                         c.cerr, hs, c.cs);
+                         c.cerr, hs, c.itol_rule, c.cs);
     cudaGraph_t out = nullptr;
     ok(cudaStreamEndCapture(c.cs, &out), "sweep capture end");
   }
@@ -1704,6 +1717,15 @@ st_status setup_context(st_handle* h, Component& c) {
     st_status s = c.inner64 ? prepare_work<double>(h, c) : prepare_work<float>(h, c);
     if (s != ST_OK) return s;
     if (!c.direct) {
+      // the inner tolerance of the sweeps: FP64 inner solves tighten only as
+      // far as the next sweep needs (next_inner_tol); FP32 ones, limited by
+      // the FP32 representation of the correction, keep their tolerance
+      c.itol = h->alloc<double>(1);
+      ST_NEED(h, c.itol);
+      const double base = inner_tol(h, c.inner64 ? 8 : 4);
+      c.itol_rule = InnerTol{c.itol, base, std::max(10.0, 10.0 * c.td->eig.cond_est),
+                             (c.inner64 && h->opt.inner_tol <= 0.0) ? 1 : 0};
+      launch_set_scalar(c.itol, base, c.cs);
       if (h->opt.autotune >= 0) {
         s = c.inner64 ? tune_component<double>(h, c) : tune_component<float>(h, c);
         if (s != ST_OK) return s;
