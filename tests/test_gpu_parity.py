@@ -433,3 +433,20 @@ def test_graph_batch_of_32_instances_matches_the_oracle():
     finally:
         for s in solvers:
             s.close()
+
+
+@pytest.mark.parametrize("body", [0, 4])
+def test_tight_target_takes_later_sweeps_with_adaptive_inner_tolerance(body):
+    """A backward-error target of 1e-15 needs a second FP64 sweep on the multigrid
+    components; that sweep solves only to the tolerance the remaining reduction needs
+    (next_inner_tol), on the host-driven loop and in graph solves, and still reaches
+    (or stagnates within 1e3 of) the target with the oracle's combined solution."""
+    from paper_2606_09688_gb300 import ST_FP64, Solver
+    p = W.layered_2d(8, 2)
+    with Solver(p, precision=ST_FP64, max_direct_rows=500, tol=1e-15, device_loop=body) as s:
+        info = s.solve(-1)
+        out = s.combine(6, 6).cpu().numpy()
+    assert info.status == 0 and info.sweeps >= 2 and info.backward_error < 1e-14
+    comps, sols = osolve.solve_all(p, method="schur")
+    pts, times = osolve.target_grid(p, 6, 6)
+    assert _rel(out, osolve.combine(p, comps, sols, pts, times)) < TOL64
