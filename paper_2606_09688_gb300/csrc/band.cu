@@ -150,6 +150,80 @@ __global__ void k_band_ldlt_win(cx<R>* __restrict__ F, BandLayout L, int RI, int
   }
 }
 
+// The shared-memory window of k_band_ldlt_win spread over a cluster of NC
+// CTAs, for windows that exceed one CTA's shared memory (FP64 with a half
+// bandwidth of 128: 266 KB): window slot s lives in CTA s mod NC, so every
+// update of a column happens in the CTA that holds it.  Per column each CTA
+// copies the pivot column from its owner's shared memory (distributed shared
+// memory), updates the columns it holds, and one cluster barrier orders those
+// reads and updates before the owner stores column k of L and reuses the slot
+// and before the next pivot column is read.  Every CTA reads the same pivot,
+// so all take the same number of barriers, also on a zero pivot.  Element by
+// element the same arithmetic as the single-CTA window kernel.
+template <typename R, int NC>
+__global__ void __cluster_dims__(NC, 1, 1) __launch_bounds__(256)
+    k_band_ldlt_dsm(cx<R>* __restrict__ F, BandLayout L, int RI, int NP, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int q = blockIdx.x / NC;
+  const int bw = L.bw, ld = L.ld, P = bw + 1;
+  const int nls = (P + NC - 1) / NC;  // window slots per CTA (slot s = ls NC + rank)
+  cx<R>* win = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* pc = win + (size_t)nls * P;  // this CTA's copy of the pivot column
+  const int64_t nrow = L.nrow;
+  cx<R>* Fq = F + (int64_t)q * L.mstride;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const cx<R> zero = mk<R>(0, 0);
+  for (int e = tid; e < nls * P; e += nth) {
+    const int ls = e / P, t = e - ls * P;
+    const int c = ls * NC + rank;  // slot c holds column c at the start
+    win[e] = (c < P && c < nrow && c + t < nrow) ? Fq[(int64_t)c * ld + t] : zero;
+  }
+  cluster.sync();
+  int slot0 = 0;  // k mod P
+  for (int64_t k = 0; k < nrow; ++k) {
+    const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
+    const int own = slot0 % NC;
+    const cx<R>* src = cluster.map_shared_rank(win, own) + (size_t)(slot0 / NC) * P;
+    for (int t = tid; t <= m; t += nth) pc[t] = src[t];
+    __syncthreads();
+    const cx<R> d = pc[0];
+    if (!(d.re * d.re + d.im * d.im > R(0))) {
+      if (tid == 0 && rank == 0) atomicExch(err, 1);
+      cluster.sync();  // no CTA leaves while another may still read its shared memory
+      return;
+    }
+    const cx<R> dinv = cdiv(mk<R>(1, 0), d);
+    for (int i = 1 + tid % RI; i <= m; i += RI) {
+      const cx<R> u = pc[i] * dinv;
+      for (int ls = tid / RI; ls < nls; ls += NP) {
+        const int s = ls * NC + rank;
+        if (s >= P) continue;
+        int j = s - slot0;
+        if (j < 0) j += P;
+        if (j < 1 || j > i) continue;
+        cx<R>& tgt = win[(size_t)ls * P + (i - j)];
+        const cx<R> a = pc[j];
+        tgt = mk<R>(fma(-u.re, a.re, fma(u.im, a.im, tgt.re)), fma(-u.re, a.im, fma(-u.im, a.re, tgt.im)));
+      }
+    }
+    cluster.sync();
+    if (rank == own) {
+      // column k of L (with 1/d_k in place of the unit diagonal), then column
+      // k + P into the freed slot
+      const int64_t c = k + P;
+      cx<R>* slot = win + (size_t)(slot0 / NC) * P;
+      for (int t = tid; t < P; t += nth) {
+        if (t <= m) Fq[k * ld + t] = t == 0 ? dinv : pc[t] * dinv;
+        slot[t] = (c < nrow && c + t < nrow) ? Fq[c * ld + t] : zero;
+      }
+    }
+    __syncthreads();
+    slot0 = slot0 + 1 == P ? 0 : slot0 + 1;
+  }
+}
+
 // The global-memory factorisation spread over a cluster of kLdltCluster CTAs
 // per mode (bands whose window does not fit in shared memory): every CTA
 // reads column k, updates its share of the pairs (i, j) (column offsets
@@ -848,6 +922,21 @@ template <typename R, int SLOTS> void set_smem_attr_p2(size_t bytes) {
 
 constexpr size_t kMaxWindowBytes = 200 * 1024;
 
+template <typename R, int NC> void set_smem_attr_ldlt_dsm(size_t bytes) {
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (bytes > done) {
+    cudaFuncSetAttribute(k_band_ldlt_dsm<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done = bytes;
+  }
+}
+
+// Shared memory of k_band_ldlt_dsm with NC CTAs: its window slots and the pivot copy.
+inline size_t dsm_bytes(int bw, int NC, size_t elem) {
+  const size_t P = (size_t)bw + 1, nls = (P + NC - 1) / NC;
+  return (nls + 1) * P * elem;
+}
+
 template <typename R> void set_smem_attr_ldlt(size_t bytes) {
   static size_t done = 0;
   std::lock_guard<std::mutex> lock(g_attr_mu);
@@ -883,6 +972,18 @@ void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int
     const int RI = (L.bw + 31) / 32 * 32, NP = RI >= 256 ? 1 : 256 / RI;
     set_smem_attr_ldlt<R>(win_bytes);
     k_band_ldlt_win<R><<<nmodes, RI * NP, win_bytes, s>>>(F, L, RI, NP, err);
+  } else if (L.bw <= 256 && dsm_bytes(L.bw, 4, sizeof(cx<R>)) <= kMaxWindowBytes) {
+    // the window over a cluster of 4 CTAs (FP64, half bandwidth 128)
+    const int RI = (L.bw + 31) / 32 * 32, NP = 256 / RI;
+    const size_t bytes = dsm_bytes(L.bw, 4, sizeof(cx<R>));
+    set_smem_attr_ldlt_dsm<R, 4>(bytes);
+    k_band_ldlt_dsm<R, 4><<<nmodes * 4, RI * NP, bytes, s>>>(F, L, RI, NP, err);
+  } else if (L.bw <= 256 && dsm_bytes(L.bw, 8, sizeof(cx<R>)) <= kMaxWindowBytes) {
+    // over 8 CTAs (FP64, half bandwidth 241: the 15^3 grid)
+    const int RI = (L.bw + 31) / 32 * 32, NP = 256 / RI;
+    const size_t bytes = dsm_bytes(L.bw, 8, sizeof(cx<R>));
+    set_smem_attr_ldlt_dsm<R, 8>(bytes);
+    k_band_ldlt_dsm<R, 8><<<nmodes * 8, RI * NP, bytes, s>>>(F, L, RI, NP, err);
   } else if (L.bw <= 256) {
     const int RI = (L.bw + 31) / 32 * 32, NP = 256 / RI;
     k_band_ldlt_cl<R><<<nmodes * kLdltCluster, RI * NP, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, RI, NP, err);
