@@ -244,7 +244,7 @@ __global__ void __cluster_dims__(kLdltCluster, 1, 1) __launch_bounds__(256)
   const int64_t nrow = L.nrow;
   cx<R>* Fq = F + (int64_t)q * L.mstride;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int i = 1 + tid % RI, p = tid / RI;
+  const int p = tid / RI;
   const int jstep = NP * kLdltCluster;
   for (int64_t k = 0; k < nrow; ++k) {
     for (int t = tid; t <= bw; t += nth) col[t] = (k + t < nrow) ? Fq[k * ld + t] : mk<R>(0, 0);
@@ -256,9 +256,26 @@ __global__ void __cluster_dims__(kLdltCluster, 1, 1) __launch_bounds__(256)
     }
     const cx<R> dinv = cdiv(mk<R>(1, 0), d);
     const int m = (int)((nrow - 1 - k) < (int64_t)bw ? (nrow - 1 - k) : bw);
-    if (i <= m) {
+    // row offsets i = 1 + tid mod RI, + RI, ... (bands wider than the CTA take several)
+    for (int i = 1 + tid % RI; i <= m; i += RI) {
       const cx<R> u = col[i] * dinv;
-      for (int j = 1 + rank + kLdltCluster * p; j <= i; j += jstep) {
+      int j = 1 + rank + kLdltCluster * p;
+      // four column offsets at a time: their four target words are loaded
+      // before any is stored (distinct columns), so four requests are in flight
+      for (; j + 3 * jstep <= i; j += 4 * jstep) {
+        cx<R>* tg[4];
+        cx<R> v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tg[r] = Fq + (k + j + r * jstep) * ld + (i - j - r * jstep);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = *tg[r];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const cx<R> a = col[j + r * jstep];
+          *tg[r] = mk<R>(fma(-u.re, a.re, fma(u.im, a.im, v[r].re)), fma(-u.re, a.im, fma(-u.im, a.re, v[r].im)));
+        }
+      }
+      for (; j <= i; j += jstep) {
         cx<R>& tgt = Fq[(k + j) * ld + (i - j)];
         const cx<R> a = col[j];
         tgt = mk<R>(fma(-u.re, a.re, fma(u.im, a.im, tgt.re)), fma(-u.re, a.im, fma(-u.im, a.re, tgt.im)));
@@ -984,8 +1001,9 @@ void launch_band_factor(cx<R>* F, cx<R>* G, const BandLayout& L, int nmodes, int
     const size_t bytes = dsm_bytes(L.bw, 8, sizeof(cx<R>));
     set_smem_attr_ldlt_dsm<R, 8>(bytes);
     k_band_ldlt_dsm<R, 8><<<nmodes * 8, RI * NP, bytes, s>>>(F, L, RI, NP, err);
-  } else if (L.bw <= 256) {
-    const int RI = (L.bw + 31) / 32 * 32, NP = 256 / RI;
+  } else if (L.bw <= 1024) {
+    // global memory, four CTAs per mode (the 31^3 grids: half bandwidth 993)
+    const int RI = L.bw <= 256 ? (L.bw + 31) / 32 * 32 : 256, NP = 256 / RI;
     k_band_ldlt_cl<R><<<nmodes * kLdltCluster, RI * NP, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, RI, NP, err);
   } else {
     k_band_ldlt<R><<<nmodes, 256, (L.bw + 1) * sizeof(cx<R>), s>>>(F, L, err);
