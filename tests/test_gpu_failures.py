@@ -11,6 +11,10 @@
   land and returns; the solve reports ST_ERR_TIMEOUT.  Nothing is left in
   flight, and the context stays usable: the same problem solved afterwards
   matches the oracle.
+* Bad data: c^2 that is NaN somewhere is refused at set-up (ST_ERR_ARG); a
+  source whose values are NaN makes the COCG status words report a non-finite
+  value, and the solve returns ST_ERR_NUMERIC (host-driven loop and graph
+  solves alike), after which a clean handle solves normally.
 """
 import numpy as np
 import pytest
@@ -90,3 +94,28 @@ def test_bounded_copy_wait_runs_out_and_context_stays_usable(device_loop):
     pts, times = osolve.target_grid(p, 4, 4)
     ref = osolve.combine(p, comps, sols, pts, times)
     assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_nan_speed_is_refused_at_setup():
+    from paper_2606_09688_gb300 import Solver, StError
+    from paper_2606_09688_gb300 import st as B
+    p = W.layered_2d(6, 2)
+    bad = W.Problem(**{**p.__dict__, "c2": lambda x: np.where(x[:, 0] > 0.7, np.nan, 1.0)})
+    with pytest.raises(StError) as e:
+        Solver(bad)
+    assert e.value.code == B.ST_ERR_ARG
+
+
+@pytest.mark.parametrize("device_loop", [0, 4])
+def test_nan_source_reports_numeric_error_and_context_stays_usable(device_loop):
+    from paper_2606_09688_gb300 import Solver, StError
+    from paper_2606_09688_gb300 import st as B
+    p = W.layered_2d(8, 2)
+    g, s_t = p.terms[0]
+    bad = W.Problem(**{**p.__dict__, "terms": [(lambda x: g(x) * np.nan, s_t)]})
+    with Solver(bad, max_direct_rows=500, device_loop=device_loop) as s:
+        with pytest.raises(StError) as e:
+            s.solve(_component(s, 6, 2))           # a multigrid component
+        assert e.value.code == B.ST_ERR_NUMERIC
+    with Solver(p, max_direct_rows=500, device_loop=device_loop) as s:
+        assert s.solve(_component(s, 6, 2)).status == 0
