@@ -21,9 +21,9 @@ def space_dofs(d: int, jx: int) -> int:
     return ((1 << jx) - 1) ** d
 
 
-def time_dofs(jt: int) -> int:
-    """dim V_jt for C^1 quadratic splines with w(0) = 0: 2^jt + 1."""
-    return (1 << jt) + 1
+def time_dofs(jt: int, p: int = 2) -> int:
+    """dim V_jt for splines of degree p and maximal regularity with w(0) = 0: 2^jt + p - 1."""
+    return (1 << jt) + p - 1
 
 
 def sparse_dofs(d: int, J: int, mx: int, mt: int) -> int:

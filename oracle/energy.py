@@ -36,8 +36,9 @@ def component_derivatives(problem, jx, jt, U, pts, times):
     shapes (len(times), len(pts)) and (len(times), len(pts), d)."""
     from .solve import _nodal, all_node_values
     N_t = 1 << jt
-    P0 = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 0)
-    P1 = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 1)
+    pt = getattr(problem, "pt", 2)
+    P0 = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 0, pt)
+    P1 = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 1, pt)
     lift = _nodal(problem.u0, space.node_coords(problem.d, problem.lo, problem.hi, jx))
     dt = np.zeros((len(times), len(pts)))
     gr = np.zeros((len(times), len(pts), problem.d))

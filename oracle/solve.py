@@ -24,6 +24,11 @@ import scipy.sparse.linalg as spl
 from . import combination, space, timebasis, timemats
 
 
+def _pt(problem):
+    """Spline degree p_t of the time space (2 unless the problem states another)."""
+    return getattr(problem, "pt", 2)
+
+
 def _nodal(fn, pts):
     return np.zeros(len(pts)) if fn is None else np.asarray(fn(pts), dtype=np.float64)
 
@@ -33,24 +38,25 @@ def rhs(problem, jx, jt, sm=None):
     sm = sm or space.space_matrices(problem, jx)
     pts = space.node_coords(problem.d, problem.lo, problem.hi, jx)
     T = problem.T
-    nt = timebasis.n_time_dofs(jt)
+    pt = _pt(problem)
+    nt = timebasis.n_time_dofs(jt, pt)
     F = np.zeros((nt, len(sm["inner"])))
     for g, s in problem.terms:
-        F += np.outer(timemats.load_separable(s, jt, T), sm["M_load"] @ _nodal(g, pts))
+        F += np.outer(timemats.load_separable(s, jt, T, pt), sm["M_load"] @ _nodal(g, pts))
     if problem.f_general is not None:
-        tq, Q = timemats.quadrature_rows(jt, T)
+        tq, Q = timemats.quadrature_rows(jt, T, pt)
         for q, tt in enumerate(tq):
             F += np.outer(Q[:, q], sm["M_load"] @ _nodal(lambda x: problem.f_general(x, tt), pts))
     if problem.v0 is not None:
-        F += np.outer(timemats.dpsi_at_zero(jt, T), sm["M_load"] @ _nodal(problem.v0, pts))
+        F += np.outer(timemats.dpsi_at_zero(jt, T, pt), sm["M_load"] @ _nodal(problem.v0, pts))
     if problem.u0 is not None:
-        F -= np.outer(timemats.load_one(jt, T), sm["K_load"] @ _nodal(problem.u0, pts))
+        F -= np.outer(timemats.load_one(jt, T, pt), sm["K_load"] @ _nodal(problem.u0, pts))
     return F
 
 
 def system_matrix(problem, jx, jt, sm=None):
     sm = sm or space.space_matrices(problem, jx)
-    A, B = timemats.time_matrices(jt, problem.T)
+    A, B = timemats.time_matrices(jt, problem.T, _pt(problem))
     return (sp.kron(sp.csr_matrix(A), sm["M"]) + sp.kron(sp.csr_matrix(B), sm["K"])).tocsc()
 
 
@@ -61,7 +67,7 @@ def apply_system(problem, jx, jt, U, sm=None):
     sum_j A[i,j] M u_j + B[i,j] K u_j (Eq. (30)), i.e. A U M^T + B U K^T in
     matrix form; M and K are symmetric.  Returns shape (n_t, N_x)."""
     sm = sm or space.space_matrices(problem, jx)
-    A, B = timemats.time_matrices(jt, problem.T)
+    A, B = timemats.time_matrices(jt, problem.T, _pt(problem))
     UM = (sm["M"] @ U.T).T
     UK = (sm["K"] @ U.T).T
     return A @ UM + B @ UK
@@ -73,7 +79,7 @@ def system_norm1(problem, jx, jt, sm=None):
     Column (j, b) holds the blocks A[i,j] M[:, b] + B[i,j] K[:, b] for every
     time row i, so its absolute sum is sum_i colsum|A[i,j] M + B[i,j] K|[b]."""
     sm = sm or space.space_matrices(problem, jx)
-    A, B = timemats.time_matrices(jt, problem.T)
+    A, B = timemats.time_matrices(jt, problem.T, _pt(problem))
     M, K = sm["M"].tocsr(), sm["K"].tocsr()
     M.sort_indices()
     K.sort_indices()
@@ -122,7 +128,7 @@ def solve_component(problem, jx, jt, F=None, method="lu"):
         S = system_matrix(problem, jx, jt, sm)
         return spl.splu(S).solve(F.ravel()).reshape(nt, nx)
     if method == "schur":
-        A, B = timemats.time_matrices(jt, problem.T)
+        A, B = timemats.time_matrices(jt, problem.T, _pt(problem))
         R, Q = sla.schur(np.linalg.solve(B, A).astype(complex), output="complex")
         G = Q.conj().T @ np.linalg.solve(B, F)
         M = sm["M"].astype(complex)
@@ -148,7 +154,7 @@ def evaluate_component(problem, jx, jt, U, pts, times):
     """u_k(x, t) = sum_i psi_i(t) (I W_i)(x) + (I_jx u0)(x) on the tensor set pts x times.
     Returns shape (len(times), len(pts))."""
     N_t = 1 << jt
-    Pt = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 0)
+    Pt = timebasis.psi(np.asarray(times, dtype=np.float64), N_t, problem.T, 0, _pt(problem))
     Wt = Pt @ U                                   # (n_times, N_x interior)
     lift = _nodal(problem.u0, space.node_coords(problem.d, problem.lo, problem.hi, jx))
     out = np.zeros((len(times), len(pts)))

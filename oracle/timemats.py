@@ -32,41 +32,41 @@ def quadrature(N: int, T: float):
     return t, wt
 
 
-def time_matrices(jt: int, T: float):
-    """(A, B) of size n_t x n_t for level jt (2^jt intervals)."""
+def time_matrices(jt: int, T: float, p: int = 2):
+    """(A, B) of size n_t x n_t for level jt (2^jt intervals), splines of degree p."""
     N = 1 << jt
     t, wt = quadrature(N, T)
     we = wt * np.exp(-t / T)
-    P = psi(t, N, T, 0)
-    P1 = psi(t, N, T, 1)
-    P2 = psi(t, N, T, 2)
+    P = psi(t, N, T, 0, p)
+    P1 = psi(t, N, T, 1, p)
+    P2 = psi(t, N, T, 2, p)
     A = P1.T @ (we[:, None] * P2)          # A[i, j] = sum_q we psi_i'(t_q) psi_j''(t_q)
     B = P1.T @ (we[:, None] * P)
-    d0 = psi(np.array([0.0]), N, T, 1)[0]
+    d0 = psi(np.array([0.0]), N, T, 1, p)[0]
     A = A + np.outer(d0, d0)
     return A, B
 
 
-def load_separable(s, jt: int, T: float) -> np.ndarray:
+def load_separable(s, jt: int, T: float, p: int = 2) -> np.ndarray:
     """b[i] = (s, psi_i')_e for a time factor s(t)."""
     N = 1 << jt
     t, wt = quadrature(N, T)
-    return psi(t, N, T, 1).T @ (wt * np.exp(-t / T) * s(t))
+    return psi(t, N, T, 1, p).T @ (wt * np.exp(-t / T) * s(t))
 
 
-def load_one(jt: int, T: float) -> np.ndarray:
+def load_one(jt: int, T: float, p: int = 2) -> np.ndarray:
     """g[i] = (1, psi_i')_e."""
-    return load_separable(lambda t: np.ones_like(t), jt, T)
+    return load_separable(lambda t: np.ones_like(t), jt, T, p)
 
 
-def dpsi_at_zero(jt: int, T: float) -> np.ndarray:
+def dpsi_at_zero(jt: int, T: float, p: int = 2) -> np.ndarray:
     """psi_i'(0)."""
-    return psi(np.array([0.0]), 1 << jt, T, 1)[0]
+    return psi(np.array([0.0]), 1 << jt, T, 1, p)[0]
 
 
-def quadrature_rows(jt: int, T: float):
+def quadrature_rows(jt: int, T: float, p: int = 2):
     """Quadrature times t_q and the matrix Q[i, q] = w_q exp(-t_q/T) psi_i'(t_q),
     so that (f(x, .), psi_i')_e = sum_q Q[i, q] f(x, t_q) for a general source."""
     N = 1 << jt
     t, wt = quadrature(N, T)
-    return t, (psi(t, N, T, 1) * (wt * np.exp(-t / T))[:, None]).T
+    return t, (psi(t, N, T, 1, p) * (wt * np.exp(-t / T))[:, None]).T

@@ -163,6 +163,8 @@ class Solver:
         import torch
         self._lib = lib()
         p = problem
+        if getattr(p, "pt", 2) != 2:
+            raise StError(ST_ERR_ARG, "the library solves C^1 quadratic time splines (pt = 2)")
         d = p.d
         keep = []  # callbacks and arrays must outlive st_setup
 

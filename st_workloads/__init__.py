@@ -53,6 +53,7 @@ class Problem:
     v0: Optional[SpaceFn] = None
     exact: Optional[SpaceTimeFn] = None   # closed-form solution, when known
     name: str = ""
+    pt: int = 2                 # degree of the time splines (maximal regularity C^{pt-1})
 
     @property
     def finest(self) -> Tuple[int, int]:
