@@ -18,6 +18,14 @@ extern "C" {
  * A[i][j] = (psi_j'', psi_i')_e + psi_j'(0) psi_i'(0), B[i][j] = (psi_j, psi_i')_e,
  * g1[i] = (1, psi_i')_e, d0[i] = psi_i'(0); n_t = 2^jt + 1. */
 st_status st_host_time_matrices(int jt, double T, double* A, double* B, double* g1, double* d0);
+/* The same matrices for time splines of degree p = 2, 3 or 4 with maximal
+ * regularity C^{p-1} (the spaces of Table "validity": proven for p = 2,
+ * conjectured for 3 and 4; dimension n_t = 2^jt + p - 1 by the formula of
+ * Section 3.2).  A and B: caller-owned host arrays of n_t x n_t doubles
+ * (row-major, row = test index); g1, d0: n_t doubles or NULL.  ST_ERR_ARG for
+ * jt outside 0..14, T <= 0, p outside 2..4 or a NULL A or B.  Host set-up
+ * math only: the solves of the library use p = 2. */
+st_status st_host_time_matrices_p(int jt, double T, int p, double* A, double* B, double* g1, double* d0);
 
 /* Eigen-decomposition of B^{-1} A used by the time eigenbasis method: the
  * kept eigenvalues (one of each conjugate pair, Im > 0, and the real ones),

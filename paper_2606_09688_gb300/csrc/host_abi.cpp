@@ -23,6 +23,21 @@ st_status st_host_time_matrices(int jt, double T, double* A, double* B, double* 
   return ST_OK;
 }
 
+st_status st_host_time_matrices_p(int jt, double T, int p, double* A, double* B, double* g1, double* d0) {
+  if (jt < 0 || jt > 14 || !(T > 0) || p < 2 || p > 4 || !A || !B) return ST_ERR_ARG;
+  TimeLevel tl;
+  build_time_level_p(jt, T, p, tl);
+  for (size_t e = 0; e < tl.A.size(); ++e) {
+    A[e] = tl.A[e];
+    B[e] = tl.B[e];
+  }
+  for (int i = 0; i < tl.nt; ++i) {
+    if (g1) g1[i] = tl.g1[i];
+    if (d0) d0[i] = tl.d0[i];
+  }
+  return ST_OK;
+}
+
 st_status st_host_time_eig(int jt, double T, int* nsel, double* lam, double* cond_est, double* resid) {
   if (jt < 0 || jt > 10 || !(T > 0) || !nsel || !lam) return ST_ERR_ARG;
   TimeLevel tl;

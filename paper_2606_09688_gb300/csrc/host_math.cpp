@@ -95,6 +95,107 @@ void build_time_level(int jt, double T, TimeLevel& tl) {
     for (int j = 0; j < 2; ++j) tl.A[(size_t)i * nt + j] += tl.d0[i] * tl.d0[j];
 }
 
+namespace {
+// Knot i of the open uniform vector of degree p on (0,T) with N intervals.
+double knot_p(int N, double T, int p, int i) {
+  if (i <= p) return 0.0;
+  if (i >= N + p) return T;
+  return (double)(i - p) * (T / N);
+}
+// Derivative of the degree-q functions of the span from the degree-(q-1)
+// quantities `lower` of the same span (B'_{i,q} = q/(t_{i+q}-t_i) B_{i,q-1}
+// - q/(t_{i+q+1}-t_{i+1}) B_{i+1,q-1}); entry r is function s - q + r.
+double dq(int N, double T, int p, int s, int q, int r, const double* lower) {
+  const int i = s - q + r;
+  double out = 0.0;
+  if (r >= 1) {
+    const double d = knot_p(N, T, p, i + q) - knot_p(N, T, p, i);
+    if (d > 0.0) out += q / d * lower[r - 1];
+  }
+  if (r <= q - 1) {
+    const double d = knot_p(N, T, p, i + q + 1) - knot_p(N, T, p, i + 1);
+    if (d > 0.0) out -= q / d * lower[r];
+  }
+  return out;
+}
+}  // namespace
+
+void bspline_local_p(int N, double T, int p, int k, double t, double* val, double* d1, double* d2) {
+  const int s = k + p;  // knot span: t_s <= t < t_{s+1}
+  // Bq[q][r] = B_{s-q+r, q}(t), the q + 1 functions of degree q non-zero on the span
+  double Bq[5][5] = {};
+  Bq[0][0] = 1.0;
+  for (int q = 1; q <= p; ++q)
+    for (int r = 0; r <= q; ++r) {
+      const int i = s - q + r;
+      double v = 0.0;
+      if (r >= 1) {
+        const double d = knot_p(N, T, p, i + q) - knot_p(N, T, p, i);
+        if (d > 0.0) v += (t - knot_p(N, T, p, i)) / d * Bq[q - 1][r - 1];
+      }
+      if (r <= q - 1) {
+        const double d = knot_p(N, T, p, i + q + 1) - knot_p(N, T, p, i + 1);
+        if (d > 0.0) v += (knot_p(N, T, p, i + q + 1) - t) / d * Bq[q - 1][r];
+      }
+      Bq[q][r] = v;
+    }
+  double dlow[5] = {};
+  for (int r = 0; r <= p - 1; ++r) dlow[r] = dq(N, T, p, s, p - 1, r, Bq[p - 2]);  // B'_{., p-1}
+  for (int a = 0; a <= p; ++a) {
+    val[a] = Bq[p][a];
+    d1[a] = dq(N, T, p, s, p, a, Bq[p - 1]);
+    d2[a] = dq(N, T, p, s, p, a, dlow);
+  }
+}
+
+void build_time_level_p(int jt, double T, int p, TimeLevel& tl) {
+  tl.jt = jt;
+  tl.N = 1 << jt;
+  tl.nt = tl.N + p - 1;
+  tl.T = T;
+  const int N = tl.N, nt = tl.nt;
+  const double h = T / N;
+  std::vector<double> gx, gw;
+  gauss_legendre(8, gx, gw);
+  const int nq = 8 * N;
+  tl.A.assign((size_t)nt * nt, 0.0);
+  tl.B.assign((size_t)nt * nt, 0.0);
+  tl.qt.assign(nq, 0.0);
+  tl.qw.assign(nq, 0.0);
+  tl.Q.assign((size_t)nt * nq, 0.0);
+  tl.g1.assign(nt, 0.0);
+  tl.d0.assign(nt, 0.0);
+  double v[5], d1[5], d2[5];
+  for (int k = 0; k < N; ++k) {
+    for (int q = 0; q < 8; ++q) {
+      const double t = k * h + 0.5 * (gx[q] + 1.0) * h;
+      const double wq = 0.5 * h * gw[q];
+      const double we = wq * std::exp(-t / T);
+      const int iq = k * 8 + q;
+      tl.qt[iq] = t;
+      tl.qw[iq] = wq;
+      bspline_local_p(N, T, p, k, t, v, d1, d2);
+      for (int a = 0; a <= p; ++a) {
+        const int i = k + a - 1;  // psi index (B_0 removed)
+        if (i < 0) continue;
+        tl.Q[(size_t)i * nq + iq] = we * d1[a];
+        tl.g1[i] += we * d1[a];
+        for (int b = 0; b <= p; ++b) {
+          const int j = k + b - 1;
+          if (j < 0) continue;
+          tl.A[(size_t)i * nt + j] += we * d1[a] * d2[b];
+          tl.B[(size_t)i * nt + j] += we * d1[a] * v[b];
+        }
+      }
+    }
+  }
+  // the penalty psi_j'(0) psi_i'(0) of A
+  bspline_local_p(N, T, p, 0, 0.0, v, d1, d2);
+  for (int a = 1; a <= p; ++a) tl.d0[a - 1] = d1[a];
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) tl.A[(size_t)i * nt + j] += tl.d0[i] * tl.d0[j];
+}
+
 bool lu_solve_real(int n, std::vector<double> A, std::vector<double>& Bm, int nrhs) {
   std::vector<int> piv(n);
   for (int k = 0; k < n; ++k) {

@@ -37,6 +37,16 @@ struct TimeLevel {
 };
 void build_time_level(int jt, double T, TimeLevel& tl);
 
+// Splines of degree p (2..4) with maximal regularity C^{p-1}: the p + 1
+// B-splines non-zero on interval k of the open uniform knot vector (p + 1
+// copies of 0 and of T) have global indices k .. k + p (B_0 first); their
+// values and first and second derivatives at t, by the Cox-de Boor recursion
+// on that interval.
+void bspline_local_p(int N, double T, int p, int k, double t, double* val, double* d1, double* d2);
+// The time level with splines of degree p (nt = N + p - 1; p = 2 gives the
+// quadratic level of build_time_level up to rounding).
+void build_time_level_p(int jt, double T, int p, TimeLevel& tl);
+
 // Eigen-decomposition of C = B^{-1} A (real, nt x nt).  Keeps one eigenvalue
 // of each complex-conjugate pair (Im > 0) and every real one; V holds the
 // matching eigenvectors (real ones scaled to be real), W the matching rows of

@@ -20,6 +20,7 @@ def lib():
     path = build.build(force=False)
     L = C.CDLL(path)
     L.st_host_time_matrices.argtypes = [C.c_int, C.c_double] + [C.c_void_p] * 4
+    L.st_host_time_matrices_p.argtypes = [C.c_int, C.c_double, C.c_int] + [C.c_void_p] * 4
     L.st_host_time_eig.argtypes = [C.c_int, C.c_double, C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]
     L.st_host_components.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p]
@@ -53,6 +54,31 @@ def test_time_matrices_match_oracle(lib, jt, T):
     assert np.allclose(B, Bo, rtol=1e-13, atol=1e-13 * np.abs(Bo).max())
     assert np.allclose(g1, timemats.load_one(jt, T), atol=1e-14)
     assert np.allclose(d0, timemats.dpsi_at_zero(jt, T), atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("jt,T", [(0, 1.0), (2, 1.0), (4, 2.5), (6, 1.0)])
+def test_degree_p_time_matrices_match_oracle(lib, p, jt, T):
+    """The library's host set-up math for time splines of degree p (maximal
+    regularity) against the oracle's (Cox-de Boor on the whole knot vector, pinned in
+    tests/test_oracle_time_degree.py); p = 2 also equals the quadratic routine."""
+    nt = (1 << jt) + p - 1
+    A, B = np.zeros((nt, nt)), np.zeros((nt, nt))
+    g1, d0 = np.zeros(nt), np.zeros(nt)
+    assert lib.st_host_time_matrices_p(jt, T, p, _ptr(A), _ptr(B), _ptr(g1), _ptr(d0)) == 0
+    Ao, Bo = timemats.time_matrices(jt, T, p)
+    assert np.allclose(A, Ao, rtol=1e-13, atol=1e-13 * np.abs(Ao).max())
+    assert np.allclose(B, Bo, rtol=1e-13, atol=1e-13 * np.abs(Bo).max())
+    assert np.allclose(g1, timemats.load_one(jt, T, p), atol=1e-14)
+    assert np.allclose(d0, timemats.dpsi_at_zero(jt, T, p), atol=1e-12)
+    if p == 2:
+        A2, B2 = np.zeros((nt, nt)), np.zeros((nt, nt))
+        assert lib.st_host_time_matrices(jt, T, _ptr(A2), _ptr(B2), None, None) == 0
+        assert np.allclose(A, A2, rtol=1e-14, atol=1e-14 * np.abs(A2).max())
+        assert np.allclose(B, B2, rtol=1e-14, atol=1e-14 * np.abs(B2).max())
+    A1 = np.zeros((nt, nt))
+    for bad in ((jt, T, 1), (jt, T, 5), (jt, -1.0, p), (15, T, p)):
+        assert lib.st_host_time_matrices_p(bad[0], bad[1], bad[2], _ptr(A1), _ptr(A1), None, None) == 1
 
 
 @pytest.mark.parametrize("J,mx,mt", [(0, 1, 1), (3, 2, 1), (8, 2, 2)])
