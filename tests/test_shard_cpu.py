@@ -100,7 +100,7 @@ def _rank_main(rank, world, port, target, results):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_sharded_combination_gloo_matches_the_full_sum(world):
     from oracle import solve as S
     target = (4, 4)
