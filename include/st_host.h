@@ -33,6 +33,11 @@ st_status st_host_time_matrices_p(int jt, double T, int p, double* A, double* B,
  * the 1-norm condition estimate of the eigenvector matrix and the relative
  * eigen-residual. */
 st_status st_host_time_eig(int jt, double T, int* nsel, double* lam, double* cond_est, double* resid);
+/* The same eigen-decomposition for time splines of degree p = 2, 3 or 4
+ * (n_t = 2^jt + p - 1; lam holds 2 n_t doubles).  ST_ERR_ARG for jt outside
+ * 0..10, T <= 0, p outside 2..4 or NULL nsel / lam; ST_ERR_NUMERIC when the
+ * QR iteration does not converge.  Host set-up math only. */
+st_status st_host_time_eig_p(int jt, double T, int p, int* nsel, double* lam, double* cond_est, double* resid);
 
 /* Component list of Eq. (19): out[3k .. 3k+2] = (j_x, j_t, coefficient), k < 2J+1. */
 st_status st_host_components(int J, int mx, int mt, int* out);

@@ -54,6 +54,22 @@ st_status st_host_time_eig(int jt, double T, int* nsel, double* lam, double* con
   return ST_OK;
 }
 
+st_status st_host_time_eig_p(int jt, double T, int p, int* nsel, double* lam, double* cond_est, double* resid) {
+  if (jt < 0 || jt > 10 || !(T > 0) || p < 2 || p > 4 || !nsel || !lam) return ST_ERR_ARG;
+  TimeLevel tl;
+  build_time_level_p(jt, T, p, tl);
+  TimeEig e;
+  if (!time_eig(tl, e)) return ST_ERR_NUMERIC;
+  *nsel = e.nsel;
+  for (int q = 0; q < e.nsel; ++q) {
+    lam[2 * q] = e.lam[q].real();
+    lam[2 * q + 1] = e.lam[q].imag();
+  }
+  if (cond_est) *cond_est = e.cond_est;
+  if (resid) *resid = e.resid;
+  return ST_OK;
+}
+
 st_status st_host_components(int J, int mx, int mt, int* out) {
   if (J < 0 || !out) return ST_ERR_ARG;
   int k = 0;

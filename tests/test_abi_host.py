@@ -21,6 +21,8 @@ def lib():
     L = C.CDLL(path)
     L.st_host_time_matrices.argtypes = [C.c_int, C.c_double] + [C.c_void_p] * 4
     L.st_host_time_matrices_p.argtypes = [C.c_int, C.c_double, C.c_int] + [C.c_void_p] * 4
+    L.st_host_time_eig_p.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int), C.c_void_p,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.st_host_time_eig.argtypes = [C.c_int, C.c_double, C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]
     L.st_host_components.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p]
@@ -105,6 +107,30 @@ def test_time_eigenvalues_match_numpy(lib, jt):
         assert np.min(np.abs(full - z)) < 1e-9 * scale
     assert res.value < 1e-12
     assert cond.value < 1e7
+
+
+@pytest.mark.parametrize("p", [3, 4])
+@pytest.mark.parametrize("jt", [1, 3, 5])
+def test_degree_p_time_eigenvalues_match_numpy(lib, p, jt):
+    """The time eigenbasis of the degree-p splines: every eigenvalue of B^{-1} A of the
+    oracle's matrices, one of each conjugate pair kept, small residual.  The eigenvalues
+    are only determined to about cond(V) eps ||C|| (Bauer-Fike), so the tolerance grows
+    with the routine's condition estimate (3e8 for p = 4 at jt = 5)."""
+    nt = (1 << jt) + p - 1
+    lam = np.zeros(2 * nt)
+    nsel, cond, res = C.c_int(), C.c_double(), C.c_double()
+    assert lib.st_host_time_eig_p(jt, 1.0, p, C.byref(nsel), _ptr(lam), C.byref(cond), C.byref(res)) == 0
+    got = lam[:2 * nsel.value].reshape(-1, 2)
+    got = got[:, 0] + 1j * got[:, 1]
+    A, B = timemats.time_matrices(jt, 1.0, p)
+    ref = np.linalg.eigvals(np.linalg.solve(B, A))
+    full = np.concatenate([got, np.conj(got[np.abs(got.imag) > 0])])
+    assert len(full) == nt
+    tol = max(1e-9, 100 * cond.value * np.finfo(float).eps) * np.abs(ref).max()
+    for z in ref:
+        assert np.min(np.abs(full - z)) < tol
+    assert res.value < 1e-12
+    assert lib.st_host_time_eig_p(jt, 1.0, 5, C.byref(nsel), _ptr(lam), None, None) == 1
 
 
 def test_generalised_symmetric_eig_matches_scipy(lib):
