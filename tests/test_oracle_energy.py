@@ -9,7 +9,10 @@
 * Convergence: the relative energy error of u^CF on the travelling wave decreases
   under refinement and stays bounded over [0, T].
 """
+import dataclasses
+
 import numpy as np
+import pytest
 
 import st_workloads as W
 from oracle import energy, solve as osolve, space
@@ -75,3 +78,21 @@ def test_energy_error_of_the_combination_decreases_and_stays_bounded():
         errs.append(np.abs(E - Eex) / Eex)
     assert np.max(errs[2]) < np.max(errs[1]) < np.max(errs[0])
     assert np.max(errs[2]) < 0.05
+
+
+@pytest.mark.parametrize("pt", [3, 4])
+def test_energy_error_with_higher_time_degree_decreases(pt):
+    """The same energy study with time splines of degree 3 and 4 (maximal regularity):
+    the relative error of E(t; u^CF) against the conserved exact energy falls with
+    the level and stays small, as for quadratic splines."""
+    times = np.linspace(0.0, 1.0, 21)
+    errs = []
+    for J in (3, 4, 5):
+        base = W.travelling_wave(J)
+        p = dataclasses.replace(base, pt=pt)
+        comps, sols = osolve.solve_all(p)
+        jq = max(jx for jx, _, _ in comps)
+        E = energy.energy_cf(p, comps, sols, jq, times)
+        Eex = energy.energy_of(p, base.exact_dt, base.exact_grad, jq + 2, times[:1])[0]
+        errs.append(np.max(np.abs(E - Eex) / Eex))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.05, errs
